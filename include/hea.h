@@ -1,0 +1,210 @@
+/*
+ * hea.h -- C ABI of libhea: GPU (sm_103a) hot path of the short-range-order (SRO) targeted
+ * structure search of Niu & Liu, "Short-Range Order Based Ultra Fast Large-Scale Modeling of
+ * High-Entropy Alloys" (arXiv 2411.18906).
+ *
+ * The library computes, on one GPU:
+ *   - a seeded random initial configuration with an exact composition           (Sec. 4.1)
+ *   - Warren-Cowley pair counts N_ij^(k) and alpha_ij^(k) = 1 - P_ij^(k) / c_j   (Sec. 4.3, Eq. sro)
+ *   - the fitness F = sqrt(sum_k w_k sum_ij (alpha - alpha_target)^2)           (Sec. 4.4, Eq. fitness_function)
+ *   - the incremental change of the counts and of F^2 for candidate swaps       (Sec. 4.5; Sec. 4.6.2)
+ *   - the parallel Monte Carlo search: K random two-atom swaps per step, best-of-K
+ *     (or non-overlapping multi-swap) accept, depth counter, step budget       (Sec. 4.2, Alg. parallel_mc;
+ *                                                                               Sec. 4.6.3-4.6.4)
+ *
+ * Conventions shared by every call:
+ *   - Pointers marked "device" are CUDA device (or managed) memory owned by the caller; pointers
+ *     marked "host" are ordinary host memory read during the call only.  The library keeps no
+ *     pointer after a call returns and never allocates device memory.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = the legacy default stream).  Device work
+ *     is asynchronous on that stream; outputs are valid after the stream is synchronised.
+ *   - Every call returns a hea_status.  Argument errors are detected on the host before any launch
+ *     and leave outputs untouched; hea_last_error() then returns a message (thread-local).
+ *     Conditions met on the device (a search that ran out of its time budget) are reported in the
+ *     status field of hea_search_result.
+ *   - Geometry: integer coordinates in half lattice units.  FCC sites are the points with X+Y+Z
+ *     even, BCC sites the points whose three coordinates share one parity; the period along each
+ *     axis is 2*L.  Site index = ((b * Lz + cz) * Ly + cy) * Lx + cx with the basis (sublattice)
+ *     b in the order FCC (0,0,0),(0,1,1),(1,0,1),(1,1,0); BCC (0,0,0),(1,1,1).  Shell k (1-based)
+ *     is the k-th smallest neighbour distance: FCC Z = 12, 6, 24, 12, 24; BCC Z = 8, 6, 12, 24, 8.
+ *   - Counts are int32 arrays [M][S][S] (row-major shell k, species i, species j); N_ij^(k) counts
+ *     ordered (site, shell vector) pairs, so row i sums to N_i * Z_k.
+ *   - Objective arithmetic (IEEE binary64, shared exactly with the reference definition):
+ *       Q = N / ((Z_k * N_i) * N_j), e = (1 - n * Q) - t, F^2 = sum over (k,i,j) row-major of
+ *       w_k * (e * e); swap key D = change of F^2 = sum over (k,i,j) row-major of
+ *       fma(dN, fma(a, dN, b), D) with a = w_k * (Q * Q) and b = -2 * (w_k * (Q * e)).
+ */
+#ifndef HEA_H
+#define HEA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Every declaration below is exported from libhea.so even though the library is built with
+ * hidden default visibility. */
+#if defined(__GNUC__)
+#pragma GCC visibility push(default)
+#endif
+
+typedef enum {
+    HEA_OK = 0,
+    HEA_EINVAL = 1,    /* invalid argument (shape, range, composition, null pointer) */
+    HEA_ENOMEM = 2,    /* problem does not fit the on-chip (shared-memory) budget of a kernel */
+    HEA_ECUDA = 3,     /* a CUDA runtime call failed (no device, launch error) */
+    HEA_ETIMEOUT = 4,  /* a search stopped at its time budget (reported in hea_search_result) */
+    HEA_EMISMATCH = 5  /* reserved: internal consistency check failed */
+} hea_status;
+
+typedef enum { HEA_FCC = 0, HEA_BCC = 1 } hea_kind;
+
+/* Opaque, host-side lattice description (no device memory behind it). */
+typedef struct hea_lattice hea_lattice;
+
+/* Maximum sizes accepted by the calls below. */
+#define HEA_MAX_SPECIES 8
+#define HEA_MAX_SHELLS 5
+#define HEA_MAX_SITES (1 << 30)
+
+/*
+ * Builds the periodic FCC/BCC supercell of Lx x Ly x Lz conventional cells (Table 1 caption:
+ * S = A * L^3 with A = 4 for fcc and 2 for bcc; non-cubic cells allowed) with shells 1..n_shells.
+ * Requires Lx, Ly, Lz >= 2 (no site is its own neighbour) and 1 <= n_shells <= 5.
+ * Host only.  *out receives a handle to release with hea_lattice_destroy.
+ */
+hea_status hea_build_lattice(int kind, int Lx, int Ly, int Lz, int n_shells, hea_lattice** out);
+void hea_lattice_destroy(hea_lattice* lat);
+int64_t hea_num_sites(const hea_lattice* lat);
+int hea_num_shells(const hea_lattice* lat);
+/* Coordination number Z_k of shell k (1-based); 0 when k is out of range. */
+int hea_shell_size(const hea_lattice* lat, int k);
+
+/*
+ * Initial configuration (Sec. 4.1: the first candidate solutions are generated entirely at
+ * random) with exactly n_per[s] sites of species s.  Sites are ordered by the unique 64-bit key
+ * (r0 << 32 | i), r0 the first word of Philox4x32-10 with key (lo32(seed), hi32(seed)) and counter
+ * (i, 0, 0, 0); the site of rank r gets species s with cum[s] <= r < cum[s+1].
+ *   n_per   host int64[S], each >= 0, summing to N
+ *   types   device uint8[N], overwritten
+ * Errors: HEA_EINVAL for a bad composition or S outside [1, 255].
+ */
+hea_status hea_init_config(const hea_lattice* lat, int S, const int64_t* n_per, uint64_t seed, uint8_t* types,
+                           void* stream);
+
+/*
+ * Full recount of the Warren-Cowley pair counts N_ij^(k) (Sec. 4.3) for n_configs
+ * configurations of the same lattice.
+ *   types   device uint8[n_configs][N], species in [0, S)
+ *   counts  device int32[n_configs][M][S][S], overwritten
+ * Errors: HEA_EINVAL for S outside [1, 8] or n_configs < 1.  Species values >= S are not checked
+ * on the device; their pairs are not counted.
+ */
+hea_status hea_sro_counts(const hea_lattice* lat, int n_configs, const uint8_t* types, int S, int32_t* counts,
+                          void* stream);
+
+/* Objective of Eq. fitness_function; all arrays in host memory, read during the call only. */
+typedef struct {
+    int S;                 /* species, 2..8 */
+    int M;                 /* shells, must equal the lattice's n_shells */
+    const int64_t* n_per;  /* int64[S] composition, each >= 1, summing to N */
+    const double* w;       /* double[M] shell weights w_k, finite, >= +0 */
+    const double* target;  /* double[M][S][S] target alpha (may be asymmetric), finite */
+} hea_objective;
+
+/*
+ * alpha_ij^(k) (Eq. sro) and F^2 (Eq. fitness_function, squared) from device counts.
+ *   counts  device int32[M][S][S];  alpha device double[M][S][S];  f2 device double[1]
+ */
+hea_status hea_sro_alpha(const hea_lattice* lat, const hea_objective* obj, const int32_t* counts, double* alpha,
+                         double* f2, void* stream);
+
+/*
+ * Scores K candidate swaps against one state (Sec. 4.5, Sec. 4.6.2): for each pair (a, b) the
+ * exact change dN of the counts and the key D = change of F^2.  Bonds between a and b keep their
+ * unordered species pair and contribute nothing.  A null move (a == b or equal species) gets
+ * D = +0.0 and dN = 0.
+ *   types   device uint8[N];  counts device int32[M][S][S] (must be the counts of types)
+ *   pairs   device int64[K][2], each in [0, N)
+ *   key     device double[K]
+ *   dcounts device int32[K][M][S][S] or NULL
+ * Errors: HEA_EINVAL for K < 1 or a bad objective.  Out-of-range pairs are not checked on the
+ * device; their key is set to NaN.
+ */
+hea_status hea_delta_swap(const hea_lattice* lat, const hea_objective* obj, const uint8_t* types,
+                          const int32_t* counts, const int64_t* pairs, int64_t K, double* key, int32_t* dcounts,
+                          void* stream);
+
+/* Parameters of the parallel Monte Carlo search (Alg. parallel_mc; Sec. 4.6.4). */
+typedef struct {
+    int32_t K;            /* candidate swaps (tasks) per step, 1..4096 */
+    int32_t accept_mode;  /* 0: best-of-K (argmin over (D, k)); 1: non-overlapping multi-accept */
+    int64_t max_steps;    /* step budget (>= 0) */
+    int32_t depth_limit;  /* stop once this many consecutive steps accepted nothing (0 = off) */
+    int32_t max_accept;   /* multi-accept: at most this many swaps per step (0 = unlimited) */
+    double threshold;     /* 0: accept only D < 0; > 0 also accepts non-null moves with D <= threshold */
+    uint64_t seed;        /* Philox key */
+    uint32_t chain;       /* chain id (third Philox counter word) */
+    uint32_t step0;       /* counter of the first step (resume: previous step0 + steps) */
+    int32_t depth0;       /* depth counter at entry (resume) */
+    int32_t reserved;     /* must be 0 */
+    int64_t timeout_us;   /* wall-clock budget measured on the device, 0 = none */
+} hea_search_params;
+
+/* Written by the search on the device (device or host-mapped pinned memory). */
+typedef struct {
+    int64_t steps;     /* steps executed */
+    int64_t trials;    /* candidates scored = steps * K */
+    int64_t accepted;  /* swaps applied */
+    int32_t depth;     /* depth counter at exit */
+    int32_t status;    /* HEA_OK, or HEA_ETIMEOUT when the time budget ended the search */
+    double f2;         /* F^2 of the final state (canonical order) */
+    double f;          /* sqrt(F^2) */
+} hea_search_result;
+
+/*
+ * Runs the search on one chain in a single persistent CTA (one step = K Philox-drawn swaps
+ * scored in parallel, then the accept step; candidate k of step s draws Philox with key
+ * (lo32(seed), hi32(seed)) and counter (k, s, chain, 1): a = r0 * N >> 32, b = r1 * N >> 32).
+ *   types   device uint8[N], in/out;  counts device int32[M][S][S], in/out (counts of types)
+ *   result  device (or host-mapped) hea_search_result
+ * Errors: HEA_EINVAL for bad parameters; HEA_ENOMEM when the cell and K do not fit the CTA's
+ * shared memory (about 400,000 sites at 4 bits per site, minus the candidate buffers).
+ */
+hea_status hea_search(const hea_lattice* lat, const hea_objective* obj, const hea_search_params* params,
+                      uint8_t* types, int32_t* counts, hea_search_result* result, void* stream);
+
+/*
+ * Batched search: n independent cells (any lattice, size, species and shell count) in one call,
+ * one CTA per cell, cells ordered largest first.  Two steps, so that the launch itself reads only
+ * device memory (and can be captured in a CUDA graph):
+ *   1. hea_search_batch_plan() validates every cell and writes a plan of hea_search_batch_plan_bytes(n)
+ *      bytes into host memory `plan_host`;
+ *   2. the caller copies those bytes to device memory `plan_dev` and calls hea_search_batch().
+ * plan_host must stay unchanged between the two calls; plan_dev must hold the copied plan until
+ * the launched work completes.
+ *   lats[n], objs[n], params[n]     host arrays
+ *   types[n], counts[n]             host arrays of device pointers (as for hea_search)
+ *   results                         device hea_search_result[n]
+ */
+size_t hea_search_batch_plan_bytes(int n);
+hea_status hea_search_batch_plan(int n, const hea_lattice* const* lats, const hea_objective* objs,
+                                 const hea_search_params* params, uint8_t* const* types, int32_t* const* counts,
+                                 hea_search_result* results, void* plan_host);
+hea_status hea_search_batch(const void* plan_host, const void* plan_dev, void* stream);
+
+/* Message for the last error returned on the calling thread ("" if none). */
+const char* hea_last_error(void);
+const char* hea_status_string(int status);
+
+#if defined(__GNUC__)
+#pragma GCC visibility pop
+#endif
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HEA_H */

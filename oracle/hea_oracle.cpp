@@ -26,10 +26,11 @@
 //   * Site index = ((b * Lz + cz) * Ly + cy) * Lx + cx, b the basis (sublattice) index.
 //     FCC basis (0,0,0),(0,1,1),(1,0,1),(1,1,0); BCC basis (0,0,0),(1,1,1) in half units.
 //   * Counts are taken per (site, shell vector) with multiplicity; cells need L >= 2 per axis.
-//   * Objective arithmetic (fixed so both implementations agree bit for bit, no FMA):
+//   * Objective arithmetic (fixed so both implementations agree bit for bit; no implicit FMA):
 //       Q_kij = N / ((Z_k * N_i) * N_j),  e_kij = (1 - n_kij * Q_kij) - t_kij,
 //       term_kij = w_k * (e_kij * e_kij),  F^2 = sum of terms in (k,i,j) row-major order.
-//   * Swap key D = sum over (k,i,j) row-major of [ w_k*(e'*e') - w_k*(e*e) ], e' after the swap.
+//   * Swap key D = change of F^2, written per entry as dN (a dN + b) with a = w (Q Q) and
+//     b = -2 (w (Q e)), summed over (k,i,j) row-major as D <- fma(dN, fma(a, dN, b), D).
 //     A swap is accepted only if it strictly lowers the objective (D < 0); a positive threshold
 //     additionally accepts non-null moves with D <= threshold.
 //   * Best-of-K: argmin over (D, k) with the smaller k on ties.
@@ -41,7 +42,8 @@
 //   * Initial configuration: sites ordered by the 64-bit key (r0 << 32 | i), r0 from Philox counter
 //     (i, 0, 0, 0); the site of rank r receives species s with cum[s] <= r < cum[s+1].
 //
-// Build: g++ -std=c++17 -O2 -ffp-contract=off -shared -fPIC (no FMA contraction anywhere).
+// Build: g++ -std=c++17 -O2 -ffp-contract=off -shared -fPIC: no implicit FMA contraction; the only
+// fused operations are the explicit std::fma calls of the swap key.
 
 #include <algorithm>
 #include <cmath>
@@ -335,13 +337,22 @@ bool swap_delta(const Geom& g, const Shells& sh, int S, const uint8_t* types, in
     return true;
 }
 
-// Swap key D = sum over (k,i,j) row-major of [ w_k (e')^2 - w_k e^2 ] (the change of F^2).
+// Swap key: the change of F^2 (Eq. fitness_function) caused by dN.  Per entry, with e' = e - dN Q,
+//   w (e')^2 - w e^2 = dN (a dN + b),   a = w (Q Q),   b = -2 (w (Q e))      (exact algebra),
+// summed over (k,i,j) in row-major order as a chain of fused multiply-adds:
+//   D <- fma(dN, fma(a, dN, b), D).
+// Entries with dN = 0 leave D unchanged bit for bit, so only rows and columns of the two swapped
+// species contribute.
 double swap_key(const Objective& ob, const int32_t* counts, const int32_t* dN) {
     double D = 0.0;
     for (int e = 0; e < ob.M * ob.S * ob.S; ++e) {
-        double after = entry_term(ob, e, (int64_t)counts[e] + dN[e]);
-        double before = entry_term(ob, e, counts[e]);
-        D = D + (after - before);
+        int k = e / (ob.S * ob.S);
+        double w = ob.w[k], Q = ob.Q[e];
+        double err = entry_error(ob, e, counts[e]);
+        double a = w * (Q * Q);
+        double b = -2.0 * (w * (Q * err));
+        double d = (double)dN[e];
+        D = std::fma(d, std::fma(a, d, b), D);
     }
     return D;
 }

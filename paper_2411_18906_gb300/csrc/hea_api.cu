@@ -1,0 +1,316 @@
+// hea_api.cu -- the C entry points of libhea (declared in include/hea.h): argument validation on
+// the host, descriptor set-up, kernel launches.  No device memory is allocated here.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "hea_device.cuh"
+#include "hea_internal.h"
+
+struct hea_lattice {
+    int kind, Lx, Ly, Lz, M;
+    int64_t N;
+    int Z[hea::kMaxShells];
+};
+
+namespace {
+
+thread_local char g_err[512] = "";
+
+hea_status fail(hea_status st, const char* fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof g_err, fmt, ap);
+    va_end(ap);
+    return st;
+}
+
+hea_status ok() {
+    g_err[0] = '\0';
+    return HEA_OK;
+}
+
+hea_status cuda_status(cudaError_t e, const char* what) {
+    if (e == cudaSuccess) return ok();
+    return fail(HEA_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+hea_status check_objective(const hea_lattice* lat, const hea_objective* obj) {
+    if (!obj) return fail(HEA_EINVAL, "objective is NULL");
+    if (obj->S < 2 || obj->S > HEA_MAX_SPECIES) return fail(HEA_EINVAL, "S = %d outside [2, %d]", obj->S, HEA_MAX_SPECIES);
+    if (obj->M != lat->M) return fail(HEA_EINVAL, "objective M = %d but lattice has %d shells", obj->M, lat->M);
+    if (!obj->n_per || !obj->w || !obj->target) return fail(HEA_EINVAL, "objective array is NULL");
+    int64_t total = 0;
+    for (int i = 0; i < obj->S; ++i) {
+        if (obj->n_per[i] < 1) return fail(HEA_EINVAL, "species %d has %lld sites; alpha needs N_i >= 1", i, (long long)obj->n_per[i]);
+        total += obj->n_per[i];
+    }
+    if (total != lat->N) return fail(HEA_EINVAL, "composition sums to %lld, lattice has %lld sites", (long long)total, (long long)lat->N);
+    for (int k = 0; k < obj->M; ++k)
+        if (!std::isfinite(obj->w[k]) || std::signbit(obj->w[k])) return fail(HEA_EINVAL, "weight w[%d] must be finite and >= +0", k);
+    for (int e = 0; e < obj->M * obj->S * obj->S; ++e)
+        if (!std::isfinite(obj->target[e])) return fail(HEA_EINVAL, "target[%d] is not finite", e);
+    return ok();
+}
+
+void fill_desc(const hea_lattice* lat, const hea_objective* obj, hea::ChainDesc* d) {
+    std::memset(d, 0, sizeof *d);
+    d->kind = lat->kind;
+    d->Lx = lat->Lx;
+    d->Ly = lat->Ly;
+    d->Lz = lat->Lz;
+    d->M = lat->M;
+    d->S = obj->S;
+    d->N = (int32_t)lat->N;
+    for (int i = 0; i < obj->S; ++i) d->n_per[i] = obj->n_per[i];
+    for (int k = 0; k < obj->M; ++k) d->w[k] = obj->w[k];
+    for (int e = 0; e < obj->M * obj->S * obj->S; ++e) d->target[e] = obj->target[e];
+}
+
+hea_status check_params(const hea_lattice* lat, const hea_search_params* p) {
+    if (!p) return fail(HEA_EINVAL, "search params are NULL");
+    if (p->K < 1 || p->K > hea::kMaxK) return fail(HEA_EINVAL, "K = %d outside [1, %d]", p->K, hea::kMaxK);
+    if (p->accept_mode != 0 && p->accept_mode != 1) return fail(HEA_EINVAL, "accept_mode must be 0 or 1");
+    if (p->max_steps < 0) return fail(HEA_EINVAL, "max_steps < 0");
+    if ((uint64_t)p->step0 + (uint64_t)p->max_steps > (1ull << 32)) return fail(HEA_EINVAL, "step0 + max_steps exceeds the 32-bit step counter");
+    if (p->depth_limit < 0 || p->max_accept < 0 || p->depth0 < 0) return fail(HEA_EINVAL, "negative depth_limit, max_accept or depth0");
+    if (!(p->threshold >= 0.0) || !std::isfinite(p->threshold)) return fail(HEA_EINVAL, "threshold must be finite and >= 0");
+    if (p->reserved != 0) return fail(HEA_EINVAL, "reserved field must be 0");
+    if (p->timeout_us < 0) return fail(HEA_EINVAL, "timeout_us < 0");
+    (void)lat;
+    return ok();
+}
+
+// Chooses 8- or 4-bit species storage so that the chain's shared memory fits one CTA.
+hea_status place_chain(const hea_lattice* lat, int S, const hea_search_params* p, hea::ChainDesc* d) {
+    for (int bits : {8, 4}) {
+        const hea::ChainLayout L = hea::chain_layout((int)lat->N, lat->M, S, p->K, bits, p->accept_mode);
+        if (L.total + 2048 <= hea::kSearchSmemLimit) {
+            d->bits = bits;
+            d->smem_bytes = L.total;
+            return ok();
+        }
+    }
+    return fail(HEA_ENOMEM, "cell of %lld sites with K = %d does not fit one CTA's shared memory", (long long)lat->N, p->K);
+}
+
+void fill_params(const hea_search_params* p, hea::ChainDesc* d) {
+    d->K = p->K;
+    d->accept_mode = p->accept_mode;
+    d->depth_limit = p->depth_limit;
+    d->max_accept = p->max_accept;
+    d->chain = p->chain;
+    d->step0 = p->step0;
+    d->depth0 = p->depth0;
+    d->max_steps = p->max_steps;
+    d->timeout_ns = p->timeout_us * 1000;
+    d->seed = p->seed;
+    d->threshold = p->threshold;
+}
+
+// Plan = header + descriptors sorted by lattice kind (FCC first), then largest work first.
+struct PlanHeader {
+    uint64_t magic;
+    int32_t n;
+    int32_t n_kind[2];     // cells per lattice kind
+    uint32_t smem_max[2];  // dynamic shared memory per kind
+    int32_t pad;
+};
+constexpr uint64_t kPlanMagic = 0x6865615F706C616EULL;  // "hea_plan"
+
+size_t plan_offset() { return hea::align_up(sizeof(PlanHeader), 256); }
+
+}  // namespace
+
+extern "C" {
+
+const char* hea_last_error(void) { return g_err; }
+
+const char* hea_status_string(int status) {
+    switch (status) {
+        case HEA_OK: return "ok";
+        case HEA_EINVAL: return "invalid argument";
+        case HEA_ENOMEM: return "does not fit on chip";
+        case HEA_ECUDA: return "CUDA error";
+        case HEA_ETIMEOUT: return "time budget reached";
+        case HEA_EMISMATCH: return "consistency check failed";
+        default: return "unknown status";
+    }
+}
+
+hea_status hea_build_lattice(int kind, int Lx, int Ly, int Lz, int n_shells, hea_lattice** out) {
+    if (!out) return fail(HEA_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (kind != HEA_FCC && kind != HEA_BCC) return fail(HEA_EINVAL, "kind must be HEA_FCC or HEA_BCC");
+    if (Lx < 2 || Ly < 2 || Lz < 2) return fail(HEA_EINVAL, "each of Lx, Ly, Lz must be >= 2");
+    if (n_shells < 1 || n_shells > HEA_MAX_SHELLS) return fail(HEA_EINVAL, "n_shells must be in [1, %d]", HEA_MAX_SHELLS);
+    const int64_t N = (int64_t)(kind == HEA_FCC ? 4 : 2) * Lx * Ly * Lz;
+    if (N > HEA_MAX_SITES) return fail(HEA_EINVAL, "%lld sites exceed the limit of %d", (long long)N, HEA_MAX_SITES);
+    hea_lattice* lat = new (std::nothrow) hea_lattice;
+    if (!lat) return fail(HEA_ENOMEM, "host allocation failed");
+    lat->kind = kind;
+    lat->Lx = Lx;
+    lat->Ly = Ly;
+    lat->Lz = Lz;
+    lat->M = n_shells;
+    lat->N = N;
+    constexpr hea::ShellTable fcc = hea::build_shell_table(hea::kFCC);
+    constexpr hea::ShellTable bcc = hea::build_shell_table(hea::kBCC);
+    for (int k = 0; k < hea::kMaxShells; ++k) lat->Z[k] = (kind == HEA_FCC) ? fcc.z[k] : bcc.z[k];
+    *out = lat;
+    return ok();
+}
+
+void hea_lattice_destroy(hea_lattice* lat) { delete lat; }
+
+int64_t hea_num_sites(const hea_lattice* lat) { return lat ? lat->N : -1; }
+
+int hea_num_shells(const hea_lattice* lat) { return lat ? lat->M : -1; }
+
+int hea_shell_size(const hea_lattice* lat, int k) {
+    if (!lat || k < 1 || k > lat->M) return 0;
+    return lat->Z[k - 1];
+}
+
+hea_status hea_init_config(const hea_lattice* lat, int S, const int64_t* n_per, uint64_t seed, uint8_t* types,
+                           void* stream) {
+    if (!lat || !n_per || !types) return fail(HEA_EINVAL, "NULL argument");
+    if (S < 1 || S > 255) return fail(HEA_EINVAL, "S = %d outside [1, 255]", S);
+    std::vector<int64_t> cum(S + 1, 0);
+    for (int s = 0; s < S; ++s) {
+        if (n_per[s] < 0) return fail(HEA_EINVAL, "n_per[%d] < 0", s);
+        cum[s + 1] = cum[s] + n_per[s];
+    }
+    if (cum[S] != lat->N) return fail(HEA_EINVAL, "composition sums to %lld, lattice has %lld sites", (long long)cum[S], (long long)lat->N);
+    if (S > 8 && lat->N > (1 << 16)) return fail(HEA_EINVAL, "more than 8 species is supported only up to 65536 sites");
+    return cuda_status(hea::launch_init_config(lat->kind, lat->Lx, lat->Ly, lat->Lz, S, cum.data(), seed, types,
+                                               as_stream(stream)),
+                       "hea_init_config launch");
+}
+
+hea_status hea_sro_counts(const hea_lattice* lat, int n_configs, const uint8_t* types, int S, int32_t* counts,
+                          void* stream) {
+    if (!lat || !types || !counts) return fail(HEA_EINVAL, "NULL argument");
+    if (S < 1 || S > HEA_MAX_SPECIES) return fail(HEA_EINVAL, "S = %d outside [1, %d]", S, HEA_MAX_SPECIES);
+    if (n_configs < 1 || n_configs > 65535) return fail(HEA_EINVAL, "n_configs = %d outside [1, 65535]", n_configs);
+    return cuda_status(hea::launch_sro_counts(lat->kind, lat->Lx, lat->Ly, lat->Lz, lat->M, S, n_configs, types,
+                                              counts, as_stream(stream)),
+                       "hea_sro_counts launch");
+}
+
+hea_status hea_sro_alpha(const hea_lattice* lat, const hea_objective* obj, const int32_t* counts, double* alpha,
+                         double* f2, void* stream) {
+    if (!lat || !counts || !alpha || !f2) return fail(HEA_EINVAL, "NULL argument");
+    hea_status st = check_objective(lat, obj);
+    if (st != HEA_OK) return st;
+    hea::ChainDesc d;
+    fill_desc(lat, obj, &d);
+    return cuda_status(hea::launch_sro_alpha(d, counts, alpha, f2, as_stream(stream)), "hea_sro_alpha launch");
+}
+
+hea_status hea_delta_swap(const hea_lattice* lat, const hea_objective* obj, const uint8_t* types,
+                          const int32_t* counts, const int64_t* pairs, int64_t K, double* key, int32_t* dcounts,
+                          void* stream) {
+    if (!lat || !types || !counts || !pairs || !key) return fail(HEA_EINVAL, "NULL argument");
+    if (K < 1 || K > (int64_t)1 << 31) return fail(HEA_EINVAL, "K = %lld outside [1, 2^31]", (long long)K);
+    hea_status st = check_objective(lat, obj);
+    if (st != HEA_OK) return st;
+    hea::ChainDesc d;
+    fill_desc(lat, obj, &d);
+    return cuda_status(hea::launch_delta_swap(d, types, counts, pairs, K, key, dcounts, as_stream(stream)),
+                       "hea_delta_swap launch");
+}
+
+hea_status hea_search(const hea_lattice* lat, const hea_objective* obj, const hea_search_params* params,
+                      uint8_t* types, int32_t* counts, hea_search_result* result, void* stream) {
+    if (!lat || !types || !counts || !result) return fail(HEA_EINVAL, "NULL argument");
+    hea_status st = check_objective(lat, obj);
+    if (st != HEA_OK) return st;
+    st = check_params(lat, params);
+    if (st != HEA_OK) return st;
+    hea::ChainDesc d;
+    fill_desc(lat, obj, &d);
+    fill_params(params, &d);
+    st = place_chain(lat, obj->S, params, &d);
+    if (st != HEA_OK) return st;
+    d.types = types;
+    d.counts = counts;
+    d.result = result;
+    const cudaError_t e = (d.kind == HEA_FCC) ? hea::launch_search_fcc(d, as_stream(stream))
+                                              : hea::launch_search_bcc(d, as_stream(stream));
+    return cuda_status(e, "hea_search launch");
+}
+
+size_t hea_search_batch_plan_bytes(int n) {
+    if (n < 1) return 0;
+    return plan_offset() + sizeof(hea::ChainDesc) * (size_t)n;
+}
+
+hea_status hea_search_batch_plan(int n, const hea_lattice* const* lats, const hea_objective* objs,
+                                 const hea_search_params* params, uint8_t* const* types, int32_t* const* counts,
+                                 hea_search_result* results, void* plan_host) {
+    if (n < 1 || n > 65535) return fail(HEA_EINVAL, "n = %d outside [1, 65535]", n);
+    if (!lats || !objs || !params || !types || !counts || !results || !plan_host) return fail(HEA_EINVAL, "NULL argument");
+    std::vector<hea::ChainDesc> descs((size_t)n);
+    for (int c = 0; c < n; ++c) {
+        if (!lats[c] || !types[c] || !counts[c]) return fail(HEA_EINVAL, "cell %d: NULL lattice or buffer", c);
+        hea_status st = check_objective(lats[c], &objs[c]);
+        if (st == HEA_OK) st = check_params(lats[c], &params[c]);
+        if (st == HEA_OK) {
+            fill_desc(lats[c], &objs[c], &descs[c]);
+            fill_params(&params[c], &descs[c]);
+            st = place_chain(lats[c], objs[c].S, &params[c], &descs[c]);
+        }
+        if (st != HEA_OK) {
+            char msg[512];
+            std::snprintf(msg, sizeof msg, "cell %d: %s", c, g_err);
+            return fail(st, "%s", msg);
+        }
+        descs[c].types = types[c];
+        descs[c].counts = counts[c];
+        descs[c].result = results + c;
+    }
+    // Largest cells first, so that the hardware block scheduler hands the longest chains out first.
+    std::stable_sort(descs.begin(), descs.end(), [](const hea::ChainDesc& a, const hea::ChainDesc& b) {
+        if (a.kind != b.kind) return a.kind < b.kind;
+        return (int64_t)a.N * a.K > (int64_t)b.N * b.K;
+    });
+    PlanHeader h{};
+    h.magic = kPlanMagic;
+    h.n = n;
+    for (const auto& d : descs) {
+        h.n_kind[d.kind] += 1;
+        h.smem_max[d.kind] = std::max(h.smem_max[d.kind], d.smem_bytes);
+    }
+    std::memset(plan_host, 0, plan_offset());
+    std::memcpy(plan_host, &h, sizeof h);
+    std::memcpy(static_cast<char*>(plan_host) + plan_offset(), descs.data(), sizeof(hea::ChainDesc) * descs.size());
+    return ok();
+}
+
+hea_status hea_search_batch(const void* plan_host, const void* plan_dev, void* stream) {
+    if (!plan_host || !plan_dev) return fail(HEA_EINVAL, "NULL plan");
+    PlanHeader h;
+    std::memcpy(&h, plan_host, sizeof h);
+    if (h.magic != kPlanMagic || h.n < 1) return fail(HEA_EINVAL, "plan_host is not a plan written by hea_search_batch_plan");
+    const hea::ChainDesc* descs = reinterpret_cast<const hea::ChainDesc*>(static_cast<const char*>(plan_dev) + plan_offset());
+    cudaStream_t s = as_stream(stream);
+    if (h.n_kind[0] > 0) {
+        hea_status st = cuda_status(hea::launch_search_batch_fcc(descs, h.n_kind[0], h.smem_max[0], s), "hea_search_batch launch");
+        if (st != HEA_OK) return st;
+    }
+    if (h.n_kind[1] > 0)
+        return cuda_status(hea::launch_search_batch_bcc(descs + h.n_kind[0], h.n_kind[1], h.smem_max[1], s),
+                           "hea_search_batch launch");
+    return ok();
+}
+
+}  // extern "C"

@@ -1,0 +1,261 @@
+// hea_device.cuh -- device-side building blocks of libhea (sm_103a): Philox4x32-10, lattice
+// shells, neighbour indexing computed on the fly from half-unit coordinates, packed species
+// storage.  Written for this library; it shares nothing with the CPU reference.
+#pragma once
+
+#include <cstdint>
+#include <utility>
+#include <cuda_runtime.h>
+
+namespace hea {
+
+constexpr int kFCC = 0;
+constexpr int kBCC = 1;
+constexpr int kMaxSpecies = 8;
+constexpr int kMaxShells = 5;
+constexpr int kMaxEntries = kMaxShells * kMaxSpecies * kMaxSpecies;  // M*S*S
+
+// ------------------------------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror & Shaw, SC'11).  Ten rounds of
+//   (x0, x1, x2, x3) -> (mulhi(B, x2) ^ x1 ^ k0, B*x2, mulhi(A, x0) ^ x3 ^ k1, A*x0)
+// with A = 0xD2511F53, B = 0xCD9E8D57, and the key advanced by the Weyl increments
+// (0x9E3779B9, 0xBB67AE85) after every round.
+// ------------------------------------------------------------------------------------------------
+struct Rand4 {
+    uint32_t r0, r1, r2, r3;
+};
+
+__device__ __forceinline__ Rand4 philox(uint32_t x0, uint32_t x1, uint32_t x2, uint32_t x3, uint32_t k0,
+                                        uint32_t k1) {
+#pragma unroll
+    for (int round = 0; round < 10; ++round) {
+        const uint32_t lo_a = 0xD2511F53u * x0;
+        const uint32_t hi_a = __umulhi(0xD2511F53u, x0);
+        const uint32_t lo_b = 0xCD9E8D57u * x2;
+        const uint32_t hi_b = __umulhi(0xCD9E8D57u, x2);
+        x0 = hi_b ^ x1 ^ k0;
+        x1 = lo_b;
+        x2 = hi_a ^ x3 ^ k1;
+        x3 = lo_a;
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    return Rand4{x0, x1, x2, x3};
+}
+
+// ------------------------------------------------------------------------------------------------
+// Coordination shells.  A half-unit integer vector joins two FCC sites iff its coordinate sum is
+// even, and two BCC sites iff its three coordinates share one parity.  Shell k is the k-th
+// smallest |d|^2 among such vectors; the table is built at compile time.
+// ------------------------------------------------------------------------------------------------
+struct ShellTable {
+    int z[kMaxShells];          // vectors in shell k
+    int first[kMaxShells + 1];  // index of the first vector of shell k
+    int radius2[kMaxShells];    // |d|^2 of shell k, half units^2
+    int reach[kMaxShells];      // largest |component| over shells 0..k
+    signed char v[96][3];
+};
+
+__host__ __device__ constexpr bool joins_sites(int kind, int x, int y, int z) {
+    return kind == kFCC ? (((x + y + z) & 1) == 0) : (((x & 1) == (y & 1)) && ((y & 1) == (z & 1)));
+}
+
+__host__ __device__ constexpr ShellTable build_shell_table(int kind) {
+    ShellTable t{};
+    int found = 0;
+    int n = 0;
+    int reach = 0;
+    for (int r2 = 1; r2 <= 16 && found < kMaxShells; ++r2) {
+        int here = 0;
+        for (int x = -4; x <= 4; ++x)
+            for (int y = -4; y <= 4; ++y)
+                for (int z = -4; z <= 4; ++z)
+                    if (x * x + y * y + z * z == r2 && joins_sites(kind, x, y, z)) {
+                        if (here == 0) t.first[found] = n;
+                        t.v[n][0] = (signed char)x;
+                        t.v[n][1] = (signed char)y;
+                        t.v[n][2] = (signed char)z;
+                        const int ax = x < 0 ? -x : x, ay = y < 0 ? -y : y, az = z < 0 ? -z : z;
+                        reach = ax > reach ? ax : reach;
+                        reach = ay > reach ? ay : reach;
+                        reach = az > reach ? az : reach;
+                        ++n;
+                        ++here;
+                    }
+        if (here > 0) {
+            t.z[found] = here;
+            t.radius2[found] = r2;
+            t.reach[found] = reach;
+            ++found;
+        }
+    }
+    t.first[kMaxShells] = n;
+    return t;
+}
+
+// Largest |component| of a vector in shells 1..M (at most 3 for M <= 5).
+template <int KIND, int M>
+__host__ __device__ constexpr int shell_reach() {
+    return build_shell_table(KIND).reach[M - 1];
+}
+
+template <int KIND, int M>
+__host__ __device__ constexpr int shell_total() {
+    return build_shell_table(KIND).first[M];
+}
+
+// ------------------------------------------------------------------------------------------------
+// Cell geometry.  Site index = b * V + (cz * Ly + cy) * Lx + cx (V = Lx*Ly*Lz cells).
+// Half-unit position (X, Y, Z) = (2cx + ox_b, 2cy + oy_b, 2cz + oz_b); for FCC the basis index is
+// b = 2*(X&1) + (Y&1), for BCC b = X&1.
+// ------------------------------------------------------------------------------------------------
+struct Geo {
+    int Lx, Ly, Lz;
+    int V;     // cells
+    int LxLy;
+    int N;     // sites
+};
+
+template <int KIND>
+__device__ __forceinline__ void site_coords(const Geo& g, uint32_t idx, int& X, int& Y, int& Z) {
+    const uint32_t b = idx / (uint32_t)g.V;
+    const uint32_t cell = idx - b * (uint32_t)g.V;
+    const uint32_t cz = cell / (uint32_t)g.LxLy;
+    const uint32_t rem = cell - cz * (uint32_t)g.LxLy;
+    const uint32_t cy = rem / (uint32_t)g.Lx;
+    const uint32_t cx = rem - cy * (uint32_t)g.Lx;
+    int ox, oy, oz;
+    if (KIND == kFCC) {
+        ox = (int)(b >> 1);
+        oy = (int)(b & 1);
+        oz = ox ^ oy;
+    } else {
+        ox = oy = oz = (int)b;
+    }
+    X = 2 * (int)cx + ox;
+    Y = 2 * (int)cy + oy;
+    Z = 2 * (int)cz + oz;
+}
+
+// Per-axis index contributions for offsets -R..R around one site: the neighbour at offset
+// (dx, dy, dz) has index x[dx+R] + y[dy+R] + z[dz+R].
+template <int KIND, int R>
+struct AxisTable {
+    int x[2 * R + 1], y[2 * R + 1], z[2 * R + 1];
+
+    __device__ __forceinline__ void build(const Geo& g, int X, int Y, int Z) {
+        const int PX = 2 * g.Lx, PY = 2 * g.Ly, PZ = 2 * g.Lz;
+#pragma unroll
+        for (int d = -R; d <= R; ++d) {
+            int xs = X + d, ys = Y + d, zs = Z + d;
+            if (d < 0) {
+                xs += (xs < 0) ? PX : 0;
+                ys += (ys < 0) ? PY : 0;
+                zs += (zs < 0) ? PZ : 0;
+            } else if (d > 0) {
+                xs -= (xs >= PX) ? PX : 0;
+                ys -= (ys >= PY) ? PY : 0;
+                zs -= (zs >= PZ) ? PZ : 0;
+            }
+            if (KIND == kFCC) {
+                x[d + R] = (xs >> 1) + (xs & 1) * 2 * g.V;
+                y[d + R] = (ys >> 1) * g.Lx + (ys & 1) * g.V;
+            } else {
+                x[d + R] = (xs >> 1) + (xs & 1) * g.V;
+                y[d + R] = (ys >> 1) * g.Lx;
+            }
+            z[d + R] = (zs >> 1) * g.LxLy;
+        }
+    }
+};
+
+// ------------------------------------------------------------------------------------------------
+// Species storage in shared memory: 8 bits per site, or 4 bits per site (two sites per byte,
+// even site in the low nibble) for cells that do not fit at 8 bits.
+// ------------------------------------------------------------------------------------------------
+template <int BITS>
+__device__ __forceinline__ int load_species(const uint8_t* s, uint32_t i) {
+    if (BITS == 8) return s[i];
+    return (s[i >> 1] >> ((i & 1u) << 2)) & 0xF;
+}
+
+template <int BITS>
+__device__ __forceinline__ void store_species(uint8_t* s, uint32_t i, int v) {
+    if (BITS == 8) {
+        s[i] = (uint8_t)v;
+    } else {
+        const uint32_t sh = (i & 1u) << 2;
+        s[i >> 1] = (uint8_t)((s[i >> 1] & ~(0xFu << sh)) | ((uint32_t)v << sh));
+    }
+}
+
+template <int BITS>
+__host__ __device__ constexpr uint32_t species_bytes(uint32_t N) {
+    return BITS == 8 ? N : (N + 1) / 2;
+}
+
+template <int KIND>
+struct ShellsOf {
+    static constexpr ShellTable table = build_shell_table(KIND);
+};
+
+// One-hot species increment of the neighbour reached by shell vector V (a compile-time index, so
+// the offsets are immediates and the axis table stays in registers).
+template <int KIND, int R, int V, typename OneHot>
+__device__ __forceinline__ uint64_t vector_increment(const AxisTable<KIND, R>& ax, uint32_t excl, OneHot& onehot) {
+    constexpr int dx = ShellsOf<KIND>::table.v[V][0] + R;
+    constexpr int dy = ShellsOf<KIND>::table.v[V][1] + R;
+    constexpr int dz = ShellsOf<KIND>::table.v[V][2] + R;
+    const uint32_t n = (uint32_t)(ax.x[dx] + ax.y[dy] + ax.z[dz]);
+    const uint64_t inc = onehot(n);
+    return (n != excl) ? inc : 0ull;
+}
+
+template <int KIND, int R, int FIRST, typename OneHot, int... I>
+__device__ __forceinline__ uint64_t shell_sum(const AxisTable<KIND, R>& ax, uint32_t excl, OneHot& onehot,
+                                              std::integer_sequence<int, I...>) {
+    return (0ull + ... + vector_increment<KIND, R, FIRST + I>(ax, excl, onehot));
+}
+
+template <int KIND, int R, int K, typename OneHot>
+__device__ __forceinline__ uint64_t shell_histogram(const AxisTable<KIND, R>& ax, uint32_t excl, OneHot& onehot) {
+    constexpr int first = ShellsOf<KIND>::table.first[K];
+    constexpr int z = ShellsOf<KIND>::table.z[K];
+    return shell_sum<KIND, R, first>(ax, excl, onehot, std::make_integer_sequence<int, z>{});
+}
+
+template <int KIND, int R, int MX, typename OneHot, int... K>
+__device__ __forceinline__ void all_shells(const AxisTable<KIND, R>& ax, uint32_t excl, OneHot& onehot,
+                                           uint64_t (&h)[MX], int M, std::integer_sequence<int, K...>) {
+    ((h[K] = (K < M) ? shell_histogram<KIND, R, K>(ax, excl, onehot) : 0ull), ...);
+}
+
+// Neighbour histogram of one site for shells 1..M (M <= MX): h[k] holds 8-bit counts per species
+// (field y at bits 8y..8y+7; Z_k <= 24 fits), skipping the neighbour equal to `excl`.
+// `onehot(n)` returns 1 << (8 * species(n)), or 0 for a site that must not be counted.
+template <int KIND, int MX, typename OneHot>
+__device__ __forceinline__ void neighbour_histogram_upto(const Geo& g, uint32_t site, uint32_t excl, OneHot onehot,
+                                                         uint64_t (&h)[MX], int M) {
+    constexpr int R = shell_reach<KIND, MX>();
+    int X, Y, Z;
+    site_coords<KIND>(g, site, X, Y, Z);
+    AxisTable<KIND, R> ax;
+    ax.build(g, X, Y, Z);
+    all_shells<KIND, R, MX>(ax, excl, onehot, h, M, std::make_integer_sequence<int, MX>{});
+}
+
+template <int KIND, int M, typename OneHot>
+__device__ __forceinline__ void neighbour_histogram(const Geo& g, uint32_t site, uint32_t excl, OneHot onehot,
+                                                    uint64_t (&h)[M]) {
+    neighbour_histogram_upto<KIND, M>(g, site, excl, onehot, h, M);
+}
+
+__device__ __forceinline__ int hist_field(uint64_t h, int y) { return (int)((h >> (8 * y)) & 0xFFu); }
+
+__device__ __forceinline__ uint64_t globaltimer_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+}  // namespace hea

@@ -1,0 +1,90 @@
+// hea_internal.h -- descriptors shared between libhea's host entry points and its kernels.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+
+#include "../../include/hea.h"
+
+namespace hea {
+
+constexpr int kChainThreads = 256;   // threads of one search CTA
+constexpr int kMaxK = 4096;          // candidates per step
+constexpr uint32_t kSearchSmemLimit = 227 * 1024;
+
+// Everything one search chain needs, passed by value (single chain) or from device memory
+// (batched search).  Objective tables are copied in so a launch reads no host memory.
+struct ChainDesc {
+    int32_t kind, Lx, Ly, Lz, M, S, N, bits;  // bits: species storage, 8 or 4 per site
+    int32_t K, accept_mode, depth_limit, max_accept;
+    uint32_t chain, step0;
+    int32_t depth0, pad0;
+    int64_t max_steps;
+    int64_t timeout_ns;
+    uint64_t seed;
+    double threshold;
+    int64_t n_per[8];
+    double w[5];
+    double target[5 * 8 * 8];
+    uint8_t* types;
+    int32_t* counts;
+    hea_search_result* result;
+    uint32_t smem_bytes;
+    int32_t pad1;
+};
+
+// Shared-memory layout of one search CTA (offsets in bytes from the dynamic smem base).
+struct ChainLayout {
+    uint32_t types, cnt, Q, tgt, ca, cb, fa, fb;
+    uint32_t qk, qa, qb, qlo, qD, qha, qhb, order, bitmap, acc;
+    uint32_t total;
+};
+
+__host__ __device__ inline uint32_t align_up(uint32_t x, uint32_t a) { return (x + a - 1) / a * a; }
+
+__host__ __device__ inline ChainLayout chain_layout(int N, int M, int S, int K, int bits, int accept_mode) {
+    ChainLayout L{};
+    const uint32_t E = (uint32_t)(M * S * S);
+    uint32_t o = 0;
+    L.types = o;
+    o = align_up(o + (bits == 8 ? (uint32_t)N : (uint32_t)(N + 1) / 2), 16);
+    L.cnt = o;   o = align_up(o + 4 * E, 16);
+    L.Q = o;     o = align_up(o + 8 * E, 16);
+    L.tgt = o;   o = align_up(o + 8 * E, 16);
+    L.ca = o;    o = align_up(o + 8 * E, 16);
+    L.cb = o;    o = align_up(o + 8 * E, 16);
+    L.fa = o;    o = align_up(o + 4 * E, 16);
+    L.fb = o;    o = align_up(o + 4 * E, 16);
+    L.qk = o;    o = align_up(o + 4 * (uint32_t)K, 16);
+    L.qa = o;    o = align_up(o + 4 * (uint32_t)K, 16);
+    L.qb = o;    o = align_up(o + 4 * (uint32_t)K, 16);
+    L.qlo = o;   o = align_up(o + 4 * (uint32_t)K, 16);
+    L.qD = o;    o = align_up(o + 8 * (uint32_t)K, 16);
+    L.qha = o;   o = align_up(o + 8 * (uint32_t)(K * M), 16);
+    L.qhb = o;   o = align_up(o + 8 * (uint32_t)(K * M), 16);
+    if (accept_mode == 1) {
+        L.order = o;  o = align_up(o + 4 * (uint32_t)K, 16);
+        L.acc = o;    o = align_up(o + 4 * (uint32_t)K, 16);
+        L.bitmap = o; o = align_up(o + 4 * (uint32_t)((N + 31) / 32), 16);
+    } else {
+        L.order = L.acc = L.bitmap = o;
+    }
+    L.total = o;
+    return L;
+}
+
+// Launchers implemented in the .cu files.
+cudaError_t launch_init_config(int kind, int Lx, int Ly, int Lz, int S, const int64_t* cum, uint64_t seed,
+                               uint8_t* types, cudaStream_t stream);
+cudaError_t launch_sro_counts(int kind, int Lx, int Ly, int Lz, int M, int S, int n_configs, const uint8_t* types,
+                              int32_t* counts, cudaStream_t stream);
+cudaError_t launch_sro_alpha(const ChainDesc& d, const int32_t* counts, double* alpha, double* f2,
+                             cudaStream_t stream);
+cudaError_t launch_delta_swap(const ChainDesc& d, const uint8_t* types, const int32_t* counts,
+                              const int64_t* pairs, int64_t K, double* key, int32_t* dcounts, cudaStream_t stream);
+cudaError_t launch_search_fcc(const ChainDesc& d, cudaStream_t stream);
+cudaError_t launch_search_bcc(const ChainDesc& d, cudaStream_t stream);
+cudaError_t launch_search_batch_fcc(const ChainDesc* descs_dev, int n, uint32_t smem_max, cudaStream_t stream);
+cudaError_t launch_search_batch_bcc(const ChainDesc* descs_dev, int n, uint32_t smem_max, cudaStream_t stream);
+
+}  // namespace hea

@@ -1,0 +1,5 @@
+// Persistent search kernels for FCC cells.
+#define HEA_SEARCH_KIND kFCC
+#define HEA_SEARCH_LAUNCH launch_search_fcc
+#define HEA_SEARCH_BATCH_LAUNCH launch_search_batch_fcc
+#include "hea_search_kind.inc"
