@@ -124,7 +124,7 @@ def run_ours(args):
     lat = hea.Lattice(spec.kind, spec.L, spec.M)
     obj = hea.Objective(spec.n_per, spec.weights(), spec.targets())
     N, S, M = lat.N, spec.S, spec.M
-    steps_per_call = TRIALS_PER_STEP // SEARCH_K
+    steps_per_call = args.trials // SEARCH_K
     trials_per_step = steps_per_call * SEARCH_K
     stream = torch.cuda.current_stream()
     types = torch.empty(N, dtype=torch.uint8, device="cuda")
@@ -235,7 +235,9 @@ def run_ours(args):
         "metric": METRIC, "value": value, "unit": "trials/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "u8+i32+f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "sites": N, "trials_per_step": trials_per_step, "K": SEARCH_K,
+        "config": {"workload": WORKLOAD if args.trials == TRIALS_PER_STEP else
+                   WORKLOAD.replace("1e8 swap trials", f"{trials_per_step} swap trials"),
+                   "sites": N, "trials_per_step": trials_per_step, "K": SEARCH_K,
                    "accept_mode": "multi", "l2": "flushed between timed steps (256 MiB write)",
                    "parallelism": f"replicas x{world}"},
         "roofline": roofline,
@@ -316,6 +318,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--cpu-steps", type=int, default=400, help="oracle search steps in the CPU sample")
+    ap.add_argument("--trials", type=int, default=TRIALS_PER_STEP,
+                    help="swap trials per step (workload size; the headline workload is 1e8)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":

@@ -210,6 +210,8 @@ def test_search_multi_accept_bit_exact(kind, L, M, S, K, steps, max_acc, seed):
     g, o = run_both(kind, L, M, S, n_per, w, target, seed, K=K, max_steps=steps, accept_mode=1,
                     max_accept=max_acc, seed=seed + 20)
     assert_same(g, o)
+    if N < 1000:
+        return      # closed neighbourhoods of 5 shells cover most of a tiny cell
     # Several swaps in one step: the first step alone accepts more than one.
     t = oracle.init_config(N, n_per, seed)
     cnt = oracle.counts(kind, L, M, S, t)
