@@ -26,10 +26,13 @@ sys.path.insert(0, ROOT)
 from paper_2411_18906_gb300 import workloads  # noqa: E402
 
 METRIC = "Δ-SRO swap trials/s at 256k-atom FCC; batched cells/s; p99 serve latency"
-SEARCH_K = 256           # candidates per search step
+SEARCH_K = 256           # candidates per step of the single-CTA chain (parity tests, CPU sample)
+COOP_KC = 512            # candidates per CTA per step of the cooperative chain
+COOP_TOP = 2             # best eligible candidates per CTA that enter the multi-accept walk
 TRIALS_PER_STEP = 100_000_000
 WORKLOAD = "FCC 40x40x40 (256,000 sites), 4 species 40/20/20/20, shells 1-3, annealed target, " \
-           "1e8 swap trials per step, multi-accept, K=256"
+           "1e8 swap trials per step, multi-accept, one chain over all SMs (512 candidates per CTA per " \
+           "search step, best 2 per CTA walked)"
 SM_COUNT = 152
 SM_MAX_MHZ = 2070.0
 
@@ -124,8 +127,17 @@ def run_ours(args):
     lat = hea.Lattice(spec.kind, spec.L, spec.M)
     obj = hea.Objective(spec.n_per, spec.weights(), spec.targets())
     N, S, M = lat.N, spec.S, spec.M
-    steps_per_call = args.trials // SEARCH_K
-    trials_per_step = steps_per_call * SEARCH_K
+    ctas = torch.cuda.get_device_properties(local).multi_processor_count
+    K = ctas * COOP_KC
+    steps_per_call = max(1, args.trials // K)
+    trials_per_step = steps_per_call * K
+    workspace = torch.zeros(hea.hea_search_coop_workspace_bytes(ctas), dtype=torch.uint8, device="cuda")
+
+    def search(step_seed):
+        params = hea.search_params(K, steps_per_call, accept_mode=1, group_size=COOP_KC, group_top=COOP_TOP,
+                                   seed=step_seed)
+        hea.hea_search_coop(lat, obj, params, ctas, types, counts, result, workspace, stream)
+
     stream = torch.cuda.current_stream()
     types = torch.empty(N, dtype=torch.uint8, device="cuda")
     counts = torch.empty((M, S, S), dtype=torch.int32, device="cuda")
@@ -139,8 +151,7 @@ def run_ours(args):
         hea.hea_init_config(lat, spec.n_per, step_seed, types, stream)
         hea.hea_sro_counts(lat, 1, types, S, counts, stream)
         hea.hea_sro_alpha(lat, obj, counts, alpha, f2, stream)
-        params = hea.search_params(SEARCH_K, steps_per_call, accept_mode=1, seed=step_seed)
-        hea.hea_search(lat, obj, params, types, counts, result, stream)
+        search(step_seed)
 
     for w in range(args.warmup):
         one_step(seed)
@@ -165,8 +176,7 @@ def run_ours(args):
         hea.hea_sro_counts(lat, 1, types, S, counts, stream)
         hea.hea_sro_alpha(lat, obj, counts, alpha, f2, stream)
         search_start[s].record(stream)
-        params = hea.search_params(SEARCH_K, steps_per_call, accept_mode=1, seed=seed)
-        hea.hea_search(lat, obj, params, types, counts, result, stream)
+        search(seed)
         stops[s].record(stream)
     torch.cuda.synchronize()
     if world > 1:
@@ -204,8 +214,7 @@ def run_ours(args):
         types.copy_(host_in, non_blocking=True)
         hea.hea_sro_counts(lat, 1, types, S, counts, stream)
         hea.hea_sro_alpha(lat, obj, counts, alpha, f2, stream)
-        params = hea.search_params(SEARCH_K, steps_per_call, accept_mode=1, seed=seed)
-        hea.hea_search(lat, obj, params, types, counts, result, stream)
+        search(seed)
         host_types.copy_(types, non_blocking=True)
         host_counts.copy_(counts, non_blocking=True)
         host_res.copy_(result, non_blocking=True)
@@ -224,7 +233,7 @@ def run_ours(args):
     search_s = (search_total_ms / args.steps) / 1000.0
     achieved_gbs = trials_per_step * bytes_per_trial / search_s / 1e9
     peak_gbs = SM_COUNT * 32 * peaks.get("sm_max_mhz", SM_MAX_MHZ) * 1e6 / 1e9
-    roofline = {"bound": "alu", "kernel": "search_kernel (persistent chain)",
+    roofline = {"bound": "alu", "kernel": f"coop_kernel (one chain, {ctas} CTAs)",
                 "achieved": round(achieved_gbs, 3), "peak": round(peak_gbs, 1), "unit": "GB/s",
                 "frac": achieved_gbs / peak_gbs, "traffic": None,
                 "peak_source": "shared-memory gather issue rate: 152 SMs x 32 lanes x max SM clock "
@@ -237,7 +246,7 @@ def run_ours(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "u8+i32+f64", "data": "synthetic",
         "config": {"workload": WORKLOAD if args.trials == TRIALS_PER_STEP else
                    WORKLOAD.replace("1e8 swap trials", f"{trials_per_step} swap trials"),
-                   "sites": N, "trials_per_step": trials_per_step, "K": SEARCH_K,
+                   "sites": N, "trials_per_step": trials_per_step, "K": K, "ctas": ctas, "search_steps": steps_per_call,
                    "accept_mode": "multi", "l2": "flushed between timed steps (256 MiB write)",
                    "parallelism": f"replicas x{world}"},
         "roofline": roofline,
@@ -245,11 +254,11 @@ def run_ours(args):
                 "d2h_bytes_per_step": N + 4 * M * S * S + hea.RESULT_BYTES},
         "gpu_launches": 4 * args.steps,
         "clocks": clocks,
-        "final": {"F": res["f"], "accepted": res["accepted"], "steps": res["steps"]},
+        "final": {"F": res["f"], "accepted": res["accepted"], "search_steps": res["steps"]},
         "wall_s": wall,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(args.cpu_steps)
+        line["cpu_baseline"] = cpu_baseline(args.cpu_steps, ctas)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -267,23 +276,27 @@ def oracle_free_initial(spec, N):
 # ------------------------------------------------------------------------------------------------
 # CPU oracle (baseline leg and reference arm)
 # ------------------------------------------------------------------------------------------------
-def cpu_baseline(n_steps):
-    """The plain serial oracle on a bounded sample of the same workload: init, recount, then
-    n_steps search steps of K candidates each.  Returns trials/s of the search part."""
+def cpu_baseline(n_steps, ctas=SM_COUNT):
+    """The plain serial oracle on a bounded sample of the same workload: init, recount, then n_steps
+    search steps with the benchmark's candidate set and accept rule (K = ctas x 512 candidates per
+    step, the best 2 eligible of every 512 walked).  Returns trials/s of the search part."""
     import oracle
     spec = workload_inputs()
     N = spec.N
+    K = ctas * COOP_KC
     t0 = time.perf_counter()
     types = oracle.init_config(N, spec.n_per, spec.seed)
     cnt = oracle.counts(spec.kind, spec.L, spec.M, spec.S, types)
     t1 = time.perf_counter()
     _, _, res, _ = oracle.search(spec.kind, spec.L, spec.M, spec.n_per, spec.weights(), spec.targets(), types, cnt,
-                                 K=SEARCH_K, max_steps=n_steps, accept_mode=1, seed=spec.seed)
+                                 K=K, max_steps=n_steps, accept_mode=1, group_size=COOP_KC, group_top=COOP_TOP,
+                                 seed=spec.seed)
     t2 = time.perf_counter()
     trials = res["trials"]
     return {"value": trials / (t2 - t1), "unit": "trials/s", "cores": 1, "kind": "oracle",
-            "sample": f"{n_steps} search steps x K={SEARCH_K} ({trials} trials) of the 256,000-site FCC "
-                      f"workload from a fresh random start; init + recount took {t1 - t0:.2f} s (not in value)",
+            "sample": f"{n_steps} search steps x K={K} ({trials} trials) of the 256,000-site FCC workload from "
+                      f"a fresh random start (same candidates and accept rule as the GPU run); init + recount "
+                      f"took {t1 - t0:.2f} s (not in value)",
             "seconds": t2 - t0}
 
 
@@ -293,17 +306,17 @@ def run_reference(args):
         return
     vals = []
     for _ in range(args.warmup):
-        cpu_baseline(max(1, args.cpu_steps // 10))
+        cpu_baseline(1)
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        vals.append(cpu_baseline(args.cpu_steps))
+        vals.append(cpu_baseline(max(1, args.cpu_steps // 2)))
     wall = time.perf_counter() - t0
     value = float(np.mean([v["value"] for v in vals]))
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "trials/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * wall / max(1, args.steps),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8+i32+f64",
             "data": "synthetic",
-            "config": {"workload": WORKLOAD, "sites": 256000, "K": SEARCH_K, "accept_mode": "multi",
+            "config": {"workload": WORKLOAD, "sites": 256000, "K": SM_COUNT * COOP_KC, "accept_mode": "multi",
                        "parallelism": "CPU oracle, 1 thread"},
             "cpu_baseline": {"value": value, "unit": "trials/s", "cores": 1, "kind": "oracle",
                              "sample": vals[0]["sample"] if vals else ""},
@@ -317,7 +330,7 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--cpu-steps", type=int, default=400, help="oracle search steps in the CPU sample")
+    ap.add_argument("--cpu-steps", type=int, default=12, help="oracle search steps in the CPU sample")
     ap.add_argument("--trials", type=int, default=TRIALS_PER_STEP,
                     help="swap trials per step (workload size; the headline workload is 1e8)")
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -139,7 +139,7 @@ hea_status hea_delta_swap(const hea_lattice* lat, const hea_objective* obj, cons
 
 /* Parameters of the parallel Monte Carlo search (Alg. parallel_mc; Sec. 4.6.4). */
 typedef struct {
-    int32_t K;            /* candidate swaps (tasks) per step, 1..4096 */
+    int32_t K;            /* candidate swaps (tasks) per step: 1..4096 per CTA */
     int32_t accept_mode;  /* 0: best-of-K (argmin over (D, k)); 1: non-overlapping multi-accept */
     int64_t max_steps;    /* step budget (>= 0) */
     int32_t depth_limit;  /* stop once this many consecutive steps accepted nothing (0 = off) */
@@ -149,6 +149,9 @@ typedef struct {
     uint32_t chain;       /* chain id (third Philox counter word) */
     uint32_t step0;       /* counter of the first step (resume: previous step0 + steps) */
     int32_t depth0;       /* depth counter at entry (resume) */
+    int32_t group_size;   /* multi-accept: candidate k belongs to group k / group_size (0 = one group of K) */
+    int32_t group_top;    /* multi-accept: only the group_top best eligible candidates (by (D, k)) of each
+                             group enter the walk (0 = all eligible candidates) */
     int32_t reserved;     /* must be 0 */
     int64_t timeout_us;   /* wall-clock budget measured on the device, 0 = none */
 } hea_search_params;
@@ -194,6 +197,30 @@ hea_status hea_search_batch_plan(int n, const hea_lattice* const* lats, const he
                                  const hea_search_params* params, uint8_t* const* types, int32_t* const* counts,
                                  hea_search_result* results, void* plan_host);
 hea_status hea_search_batch(const void* plan_host, const void* plan_dev, void* stream);
+
+/*
+ * Cooperative search: one chain run by `ctas` co-resident CTAs, one per SM, each holding a copy
+ * of the cell in shared memory.  The K candidates of a step are split into ctas equal slices;
+ * each CTA scores its slice, the CTAs exchange their best candidates through `workspace`
+ * behind a grid barrier, and every CTA applies the same accepted swaps.  Results are those of
+ * hea_search with the same parameters:
+ *   best-of-K (accept_mode 0): identical to hea_search for any K;
+ *   multi-accept (accept_mode 1): requires group_size = K / ctas and 1 <= group_top <= 4, and is
+ *   then identical to hea_search with those group parameters.
+ *   workspace        device memory of at least hea_search_coop_workspace_bytes(ctas) bytes,
+ *                    16-byte aligned, owned by the caller; its first 64 bytes are zeroed on
+ *                    `stream` before the launch; calls that share a workspace must not overlap
+ * Errors: HEA_EINVAL for bad parameters or a short workspace; HEA_ENOMEM when `ctas` CTAs with
+ * this cell cannot all be resident (see hea_search_coop_max_ctas).  A grid barrier that waits
+ * longer than 2 s ends the search with status HEA_ETIMEOUT in the result.
+ */
+size_t hea_search_coop_workspace_bytes(int ctas);
+/* Most CTAs that can be co-resident for this problem with `ctas`-way splitting (0 on error). */
+int hea_search_coop_max_ctas(const hea_lattice* lat, const hea_objective* obj, const hea_search_params* params,
+                             int ctas);
+hea_status hea_search_coop(const hea_lattice* lat, const hea_objective* obj, const hea_search_params* params,
+                           int ctas, uint8_t* types, int32_t* counts, hea_search_result* result, void* workspace,
+                           size_t workspace_bytes, void* stream);
 
 /* Message for the last error returned on the calling thread ("" if none). */
 const char* hea_last_error(void);

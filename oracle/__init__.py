@@ -33,6 +33,8 @@ class SearchParams(ctypes.Structure):
         ("chain", ctypes.c_uint32),
         ("step0", ctypes.c_uint32),
         ("depth0", ctypes.c_int32),
+        ("group_size", ctypes.c_int32),
+        ("group_top", ctypes.c_int32),
         ("check", ctypes.c_int32),
     ]
 
@@ -184,7 +186,8 @@ def draw_pairs(N, seed, chain, step0, n_steps, K):
 
 
 def search(kind, L, M, n_per, w, target, types, cnt, *, K, max_steps, accept_mode=0, depth_limit=0,
-           max_accept=0, threshold=0.0, seed=1, chain=0, step0=0, depth0=0, check=False, log=False):
+           max_accept=0, threshold=0.0, seed=1, chain=0, step0=0, depth0=0, group_size=0, group_top=0,
+           check=False, log=False, timeout_us=0):
     """Runs the search in place on copies; returns (types, counts, result dict, accepted pairs or None)."""
     n = np.ascontiguousarray(n_per, dtype=np.int64)
     S = len(n)
@@ -193,7 +196,7 @@ def search(kind, L, M, n_per, w, target, types, cnt, *, K, max_steps, accept_mod
     ty = np.array(types, dtype=np.uint8, copy=True)
     c = np.array(cnt, dtype=np.int32, copy=True).reshape(M, S, S)
     p = SearchParams(K, accept_mode, max_steps, depth_limit, max_accept, threshold, seed, chain, step0,
-                     depth0, 1 if check else 0)
+                     depth0, group_size, group_top, 1 if check else 0)
     r = SearchResult()
     acc = np.zeros((max(1, K * max_steps), 2), np.int64) if log else None
     rc = lib().or_search(kind, *L, M, S, _ptr(n), _ptr(w), _ptr(t), ctypes.byref(p), _ptr(ty), _ptr(c),

@@ -542,6 +542,8 @@ struct or_search_params {
     uint32_t chain;
     uint32_t step0;        // first step counter (resume)
     int32_t depth0;        // depth counter at entry (resume)
+    int32_t group_size;    // multi-accept: candidate k belongs to group k / group_size (0 = one group)
+    int32_t group_top;     // multi-accept: only the group_top best eligible of each group are walked (0 = all)
     int32_t check;         // 1 = full recount after every step, compared with the running counts
 };
 
@@ -564,7 +566,8 @@ int or_search(int kind, int Lx, int Ly, int Lz, int M, int S, const int64_t* n_p
     if (!make_geom(kind, Lx, Ly, Lz, &g) || !make_shells(g, M, &sh) ||
         !make_objective(g, sh, S, n_per, w, target, &ob))
         return OR_EINVAL;
-    if (p->K < 1 || p->max_steps < 0 || p->depth_limit < 0 || p->max_accept < 0 ||
+    if (p->K < 1 || p->max_steps < 0 || p->depth_limit < 0 || p->max_accept < 0 || p->group_size < 0 ||
+        p->group_top < 0 ||
         (p->accept_mode != 0 && p->accept_mode != 1) || !(p->threshold >= 0.0))
         return OR_EINVAL;
     const int E = M * S * S;
@@ -603,13 +606,26 @@ int or_search(int kind, int Lx, int Ly, int Lz, int M, int S, const int64_t* n_p
             }
         } else {
             // Non-overlapping multi-accept in ascending (D, k).
+            auto before = [&](int x, int y) {
+                if (D[x] != D[y]) return D[x] < D[y];
+                return x < y;
+            };
             std::vector<int> order;
             for (int k = 0; k < K; ++k)
                 if (eligible(D[k], is_null[k], p->threshold)) order.push_back(k);
-            std::sort(order.begin(), order.end(), [&](int x, int y) {
-                if (D[x] != D[y]) return D[x] < D[y];
-                return x < y;
-            });
+            if (p->group_top > 0) {
+                // Keep only the group_top best eligible candidates of each group.
+                const int G = p->group_size > 0 ? p->group_size : K;
+                std::vector<int> kept;
+                for (int c : order) {
+                    int better = 0;
+                    for (int o : order)
+                        if (o / G == c / G && before(o, c)) ++better;
+                    if (better < p->group_top) kept.push_back(c);
+                }
+                order.swap(kept);
+            }
+            std::sort(order.begin(), order.end(), before);
             std::vector<int64_t> taken;  // sites swapped this step
             for (int c : order) {
                 if (p->max_accept > 0 && n_acc >= p->max_accept) break;

@@ -77,11 +77,12 @@ void fill_desc(const hea_lattice* lat, const hea_objective* obj, hea::ChainDesc*
 
 hea_status check_params(const hea_lattice* lat, const hea_search_params* p) {
     if (!p) return fail(HEA_EINVAL, "search params are NULL");
-    if (p->K < 1 || p->K > hea::kMaxK) return fail(HEA_EINVAL, "K = %d outside [1, %d]", p->K, hea::kMaxK);
+    if (p->K < 1) return fail(HEA_EINVAL, "K = %d < 1", p->K);
     if (p->accept_mode != 0 && p->accept_mode != 1) return fail(HEA_EINVAL, "accept_mode must be 0 or 1");
     if (p->max_steps < 0) return fail(HEA_EINVAL, "max_steps < 0");
     if ((uint64_t)p->step0 + (uint64_t)p->max_steps > (1ull << 32)) return fail(HEA_EINVAL, "step0 + max_steps exceeds the 32-bit step counter");
     if (p->depth_limit < 0 || p->max_accept < 0 || p->depth0 < 0) return fail(HEA_EINVAL, "negative depth_limit, max_accept or depth0");
+    if (p->group_size < 0 || p->group_top < 0) return fail(HEA_EINVAL, "negative group_size or group_top");
     if (!(p->threshold >= 0.0) || !std::isfinite(p->threshold)) return fail(HEA_EINVAL, "threshold must be finite and >= 0");
     if (p->reserved != 0) return fail(HEA_EINVAL, "reserved field must be 0");
     if (p->timeout_us < 0) return fail(HEA_EINVAL, "timeout_us < 0");
@@ -89,17 +90,38 @@ hea_status check_params(const hea_lattice* lat, const hea_search_params* p) {
     return ok();
 }
 
-// Chooses 8- or 4-bit species storage so that the chain's shared memory fits one CTA.
-hea_status place_chain(const hea_lattice* lat, int S, const hea_search_params* p, hea::ChainDesc* d) {
+// Chooses 8- or 4-bit species storage so that the chain's shared memory (the cell plus `qcap`
+// candidate slots) fits one CTA.
+hea_status place_chain(const hea_lattice* lat, int S, const hea_search_params* p, int qcap, hea::ChainDesc* d) {
     for (int bits : {8, 4}) {
-        const hea::ChainLayout L = hea::chain_layout((int)lat->N, lat->M, S, p->K, bits, p->accept_mode);
+        const hea::ChainLayout L = hea::chain_layout((int)lat->N, lat->M, S, qcap, bits, p->accept_mode);
         if (L.total + 2048 <= hea::kSearchSmemLimit) {
             d->bits = bits;
             d->smem_bytes = L.total;
+            d->qcap = qcap;
             return ok();
         }
     }
-    return fail(HEA_ENOMEM, "cell of %lld sites with K = %d does not fit one CTA's shared memory", (long long)lat->N, p->K);
+    return fail(HEA_ENOMEM, "cell of %lld sites with %d candidate slots does not fit one CTA's shared memory",
+                (long long)lat->N, qcap);
+}
+
+// Cooperative chain: K = ctas * Kc; multi-accept needs group_size = Kc and 1 <= group_top <= 4.
+hea_status check_coop(const hea_search_params* p, int ctas, int* qcap) {
+    if (ctas < 1 || ctas > 65535) return fail(HEA_EINVAL, "ctas = %d outside [1, 65535]", ctas);
+    if (p->K % ctas != 0) return fail(HEA_EINVAL, "K = %d is not a multiple of ctas = %d", p->K, ctas);
+    const int Kc = p->K / ctas;
+    if (Kc > hea::kMaxK) return fail(HEA_EINVAL, "K / ctas = %d exceeds %d", Kc, hea::kMaxK);
+    int top = 1;
+    if (p->accept_mode == 1) {
+        if (p->group_size != Kc)
+            return fail(HEA_EINVAL, "cooperative multi-accept needs group_size = K / ctas = %d (got %d)", Kc, p->group_size);
+        if (p->group_top < 1 || p->group_top > hea::kCoopMaxTop)
+            return fail(HEA_EINVAL, "cooperative multi-accept needs 1 <= group_top <= %d", hea::kCoopMaxTop);
+        top = p->group_top;
+    }
+    *qcap = Kc > ctas * top ? Kc : ctas * top;
+    return ok();
 }
 
 void fill_params(const hea_search_params* p, hea::ChainDesc* d) {
@@ -110,6 +132,8 @@ void fill_params(const hea_search_params* p, hea::ChainDesc* d) {
     d->chain = p->chain;
     d->step0 = p->step0;
     d->depth0 = p->depth0;
+    d->group_size = p->group_size;
+    d->group_top = p->group_top;
     d->max_steps = p->max_steps;
     d->timeout_ns = p->timeout_us * 1000;
     d->seed = p->seed;
@@ -236,14 +260,16 @@ hea_status hea_search(const hea_lattice* lat, const hea_objective* obj, const he
     if (st != HEA_OK) return st;
     st = check_params(lat, params);
     if (st != HEA_OK) return st;
+    if (params->K > hea::kMaxK) return fail(HEA_EINVAL, "K = %d exceeds %d for a single-CTA chain", params->K, hea::kMaxK);
     hea::ChainDesc d;
     fill_desc(lat, obj, &d);
     fill_params(params, &d);
-    st = place_chain(lat, obj->S, params, &d);
+    st = place_chain(lat, obj->S, params, params->K, &d);
     if (st != HEA_OK) return st;
     d.types = types;
     d.counts = counts;
     d.result = result;
+    d.ctas = 1;
     const cudaError_t e = (d.kind == HEA_FCC) ? hea::launch_search_fcc(d, as_stream(stream))
                                               : hea::launch_search_bcc(d, as_stream(stream));
     return cuda_status(e, "hea_search launch");
@@ -264,10 +290,12 @@ hea_status hea_search_batch_plan(int n, const hea_lattice* const* lats, const he
         if (!lats[c] || !types[c] || !counts[c]) return fail(HEA_EINVAL, "cell %d: NULL lattice or buffer", c);
         hea_status st = check_objective(lats[c], &objs[c]);
         if (st == HEA_OK) st = check_params(lats[c], &params[c]);
+        if (st == HEA_OK && params[c].K > hea::kMaxK) st = fail(HEA_EINVAL, "K = %d exceeds %d", params[c].K, hea::kMaxK);
         if (st == HEA_OK) {
             fill_desc(lats[c], &objs[c], &descs[c]);
             fill_params(&params[c], &descs[c]);
-            st = place_chain(lats[c], objs[c].S, &params[c], &descs[c]);
+            st = place_chain(lats[c], objs[c].S, &params[c], params[c].K, &descs[c]);
+            descs[c].ctas = 1;
         }
         if (st != HEA_OK) {
             char msg[512];
@@ -311,6 +339,55 @@ hea_status hea_search_batch(const void* plan_host, const void* plan_dev, void* s
         return cuda_status(hea::launch_search_batch_bcc(descs + h.n_kind[0], h.n_kind[1], h.smem_max[1], s),
                            "hea_search_batch launch");
     return ok();
+}
+
+size_t hea_search_coop_workspace_bytes(int ctas) { return ctas < 1 ? 0 : hea::coop_workspace_bytes(ctas); }
+
+int hea_search_coop_max_ctas(const hea_lattice* lat, const hea_objective* obj, const hea_search_params* params,
+                             int ctas) {
+    if (!lat) return 0;
+    if (check_objective(lat, obj) != HEA_OK || check_params(lat, params) != HEA_OK) return 0;
+    int qcap = 0;
+    if (check_coop(params, ctas, &qcap) != HEA_OK) return 0;
+    hea::ChainDesc d;
+    fill_desc(lat, obj, &d);
+    fill_params(params, &d);
+    if (place_chain(lat, obj->S, params, qcap, &d) != HEA_OK) return 0;
+    return (d.kind == HEA_FCC) ? hea::coop_max_ctas_fcc(d) : hea::coop_max_ctas_bcc(d);
+}
+
+hea_status hea_search_coop(const hea_lattice* lat, const hea_objective* obj, const hea_search_params* params,
+                           int ctas, uint8_t* types, int32_t* counts, hea_search_result* result, void* workspace,
+                           size_t workspace_bytes, void* stream) {
+    if (!lat || !types || !counts || !result || !workspace) return fail(HEA_EINVAL, "NULL argument");
+    hea_status st = check_objective(lat, obj);
+    if (st != HEA_OK) return st;
+    st = check_params(lat, params);
+    if (st != HEA_OK) return st;
+    int qcap = 0;
+    st = check_coop(params, ctas, &qcap);
+    if (st != HEA_OK) return st;
+    if (workspace_bytes < hea::coop_workspace_bytes(ctas))
+        return fail(HEA_EINVAL, "workspace of %zu bytes is smaller than the %zu needed", workspace_bytes,
+                    hea::coop_workspace_bytes(ctas));
+    if (reinterpret_cast<uintptr_t>(workspace) % 16 != 0) return fail(HEA_EINVAL, "workspace is not 16-byte aligned");
+    hea::ChainDesc d;
+    fill_desc(lat, obj, &d);
+    fill_params(params, &d);
+    st = place_chain(lat, obj->S, params, qcap, &d);
+    if (st != HEA_OK) return st;
+    const int most = (d.kind == HEA_FCC) ? hea::coop_max_ctas_fcc(d) : hea::coop_max_ctas_bcc(d);
+    if (most < 1) return fail(HEA_ECUDA, "no CUDA device for a cooperative launch");
+    if (ctas > most) return fail(HEA_ENOMEM, "%d CTAs cannot be co-resident with %u bytes of shared memory each (at most %d)",
+                                 ctas, d.smem_bytes, most);
+    d.types = types;
+    d.counts = counts;
+    d.result = result;
+    d.ctas = ctas;
+    d.workspace = workspace;
+    const cudaError_t e = (d.kind == HEA_FCC) ? hea::launch_search_coop_fcc(d, as_stream(stream))
+                                              : hea::launch_search_coop_bcc(d, as_stream(stream));
+    return cuda_status(e, "hea_search_coop launch");
 }
 
 }  // extern "C"

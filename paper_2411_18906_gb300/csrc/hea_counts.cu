@@ -167,13 +167,7 @@ static cudaError_t launch_counts_t(const Geo& g, int S, int n_configs, const uin
 
 cudaError_t launch_sro_counts(int kind, int Lx, int Ly, int Lz, int M, int S, int n_configs, const uint8_t* types,
                               int32_t* counts, cudaStream_t stream) {
-    Geo g;
-    g.Lx = Lx;
-    g.Ly = Ly;
-    g.Lz = Lz;
-    g.V = Lx * Ly * Lz;
-    g.LxLy = Lx * Ly;
-    g.N = (kind == kFCC ? 4 : 2) * g.V;
+    const Geo g = make_geo(kind, Lx, Ly, Lz);
     cudaError_t err = cudaMemsetAsync(counts, 0, sizeof(int32_t) * (size_t)n_configs * M * S * S, stream);
     if (err != cudaSuccess) return err;
 #define HEA_COUNTS_CASE(KD, MM) \

@@ -23,13 +23,7 @@ __global__ void __launch_bounds__(256) delta_swap_kernel(const __grid_constant__
         s_cb[e] = __dmul_rn(-2.0, __dmul_rn(w, __dmul_rn(Q, err)));
     }
     __syncthreads();
-    Geo g;
-    g.Lx = d.Lx;
-    g.Ly = d.Ly;
-    g.Lz = d.Lz;
-    g.V = d.Lx * d.Ly * d.Lz;
-    g.LxLy = d.Lx * d.Ly;
-    g.N = d.N;
+    const Geo g = make_geo(KIND, d.Lx, d.Ly, d.Lz);
     const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= K) return;
     const int64_t a64 = pairs[2 * c], b64 = pairs[2 * c + 1];
@@ -55,11 +49,14 @@ __global__ void __launch_bounds__(256) delta_swap_kernel(const __grid_constant__
     uint64_t ha[M], hb[M];
     neighbour_histogram<KIND, M>(g, a, b, onehot, ha);
     neighbour_histogram<KIND, M>(g, b, a, onehot, hb);
-    key[c] = exact_key(M, S, s_ca, s_cb, A, B, ha, hb);
+    uint64_t gb[M];
+#pragma unroll
+    for (int k = 0; k < M; ++k) gb[k] = pack_g(ha[k], hb[k]);
+    key[c] = exact_key(M, S, s_ca, s_cb, A, B, gb);
     if (dc) {
         for (int e = 0; e < E; ++e) {
             const int k = e / (S * S), i = (e / S) % S, j = e % S;
-            dc[e] = entry_delta(ha[k], hb[k], A, B, i, j);
+            dc[e] = entry_delta(gb[k], A, B, i, j);
         }
     }
 }

@@ -109,20 +109,56 @@ __host__ __device__ constexpr int shell_total() {
 // Half-unit position (X, Y, Z) = (2cx + ox_b, 2cy + oy_b, 2cz + oz_b); for FCC the basis index is
 // b = 2*(X&1) + (Y&1), for BCC b = X&1.
 // ------------------------------------------------------------------------------------------------
+// Unsigned division by a runtime constant d for dividends n < 2^31 (Granlund-Montgomery):
+// n / d = umulhi(n, m) >> s with l = ceil(log2 d), m = ceil(2^(31+l) / d), s = l - 1; d = 1 uses
+// s = -1 (quotient n).  m < 2^32 because d > 2^(l-1).
+struct Divider {
+    uint32_t m;
+    int s;
+};
+
+__host__ __device__ inline Divider make_divider(uint32_t d) {
+    if (d <= 1) return Divider{0u, -1};
+    int l = 0;
+    while ((1ull << l) < (uint64_t)d) ++l;
+    const uint64_t p = 1ull << (31 + l);
+    const uint64_t m = p / d + ((p % d) != 0 ? 1ull : 0ull);
+    return Divider{(uint32_t)m, l - 1};
+}
+
+__device__ __forceinline__ uint32_t divide(uint32_t n, const Divider& v) {
+    return v.s < 0 ? n : (__umulhi(n, v.m) >> v.s);
+}
+
 struct Geo {
     int Lx, Ly, Lz;
     int V;     // cells
     int LxLy;
     int N;     // sites
+    Divider dV, dLxLy, dLx;
 };
+
+__host__ __device__ inline Geo make_geo(int kind, int Lx, int Ly, int Lz) {
+    Geo g;
+    g.Lx = Lx;
+    g.Ly = Ly;
+    g.Lz = Lz;
+    g.V = Lx * Ly * Lz;
+    g.LxLy = Lx * Ly;
+    g.N = (kind == kFCC ? 4 : 2) * g.V;
+    g.dV = make_divider((uint32_t)g.V);
+    g.dLxLy = make_divider((uint32_t)g.LxLy);
+    g.dLx = make_divider((uint32_t)Lx);
+    return g;
+}
 
 template <int KIND>
 __device__ __forceinline__ void site_coords(const Geo& g, uint32_t idx, int& X, int& Y, int& Z) {
-    const uint32_t b = idx / (uint32_t)g.V;
+    const uint32_t b = divide(idx, g.dV);
     const uint32_t cell = idx - b * (uint32_t)g.V;
-    const uint32_t cz = cell / (uint32_t)g.LxLy;
+    const uint32_t cz = divide(cell, g.dLxLy);
     const uint32_t rem = cell - cz * (uint32_t)g.LxLy;
-    const uint32_t cy = rem / (uint32_t)g.Lx;
+    const uint32_t cy = divide(rem, g.dLx);
     const uint32_t cx = rem - cy * (uint32_t)g.Lx;
     int ox, oy, oz;
     if (KIND == kFCC) {

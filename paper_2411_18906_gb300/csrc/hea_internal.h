@@ -4,12 +4,14 @@
 #include <cstddef>
 #include <cstdint>
 
-#include "../../include/hea.h"
+#include "hea.h"
 
 namespace hea {
 
-constexpr int kChainThreads = 256;   // threads of one search CTA
-constexpr int kMaxK = 4096;          // candidates per step
+constexpr int kChainThreads = 256;   // threads of a single-CTA search chain
+constexpr int kCoopThreads = 512;    // threads of each CTA of a cooperative chain
+constexpr int kMaxK = 4096;          // candidates per CTA per step
+constexpr int kCoopMaxTop = 4;       // records (best eligible candidates) per CTA per step
 constexpr uint32_t kSearchSmemLimit = 227 * 1024;
 
 // Everything one search chain needs, passed by value (single chain) or from device memory
@@ -18,7 +20,7 @@ struct ChainDesc {
     int32_t kind, Lx, Ly, Lz, M, S, N, bits;  // bits: species storage, 8 or 4 per site
     int32_t K, accept_mode, depth_limit, max_accept;
     uint32_t chain, step0;
-    int32_t depth0, pad0;
+    int32_t depth0, group_size, group_top, ctas;
     int64_t max_steps;
     int64_t timeout_ns;
     uint64_t seed;
@@ -29,48 +31,83 @@ struct ChainDesc {
     uint8_t* types;
     int32_t* counts;
     hea_search_result* result;
+    void* workspace;        // cooperative chain: exchange area (see CoopHeader)
     uint32_t smem_bytes;
-    int32_t pad1;
+    int32_t qcap;           // candidate slots in shared memory
 };
 
 // Shared-memory layout of one search CTA (offsets in bytes from the dynamic smem base).
 struct ChainLayout {
-    uint32_t types, cnt, Q, tgt, ca, cb, fa, fb;
-    uint32_t qk, qa, qb, qlo, qD, qha, qhb, order, bitmap, acc;
+    uint32_t types, cnt, Q, tgt, ca, cb, fa, fb, fQ, ft, beta, vec;
+    uint32_t qk, qa, qb, qlo, qhi, qD, qg, order, acc, bitmap;
     uint32_t total;
 };
 
 __host__ __device__ inline uint32_t align_up(uint32_t x, uint32_t a) { return (x + a - 1) / a * a; }
 
-__host__ __device__ inline ChainLayout chain_layout(int N, int M, int S, int K, int bits, int accept_mode) {
+// qcap: candidate slots (the candidates a CTA scores per step, or the merged records of a
+// cooperative chain, whichever is larger).
+__host__ __device__ inline ChainLayout chain_layout(int N, int M, int S, int qcap, int bits, int accept_mode) {
     ChainLayout L{};
     const uint32_t E = (uint32_t)(M * S * S);
+    const uint32_t C = (uint32_t)qcap;
     uint32_t o = 0;
     L.types = o;
     o = align_up(o + (bits == 8 ? (uint32_t)N : (uint32_t)(N + 1) / 2), 16);
-    L.cnt = o;   o = align_up(o + 4 * E, 16);
-    L.Q = o;     o = align_up(o + 8 * E, 16);
-    L.tgt = o;   o = align_up(o + 8 * E, 16);
-    L.ca = o;    o = align_up(o + 8 * E, 16);
-    L.cb = o;    o = align_up(o + 8 * E, 16);
-    L.fa = o;    o = align_up(o + 4 * E, 16);
-    L.fb = o;    o = align_up(o + 4 * E, 16);
-    L.qk = o;    o = align_up(o + 4 * (uint32_t)K, 16);
-    L.qa = o;    o = align_up(o + 4 * (uint32_t)K, 16);
-    L.qb = o;    o = align_up(o + 4 * (uint32_t)K, 16);
-    L.qlo = o;   o = align_up(o + 4 * (uint32_t)K, 16);
-    L.qD = o;    o = align_up(o + 8 * (uint32_t)K, 16);
-    L.qha = o;   o = align_up(o + 8 * (uint32_t)(K * M), 16);
-    L.qhb = o;   o = align_up(o + 8 * (uint32_t)(K * M), 16);
+    L.cnt = o;    o = align_up(o + 4 * E, 16);
+    L.Q = o;      o = align_up(o + 8 * E, 16);
+    L.tgt = o;    o = align_up(o + 8 * E, 16);
+    L.ca = o;     o = align_up(o + 8 * E, 16);
+    L.cb = o;     o = align_up(o + 8 * E, 16);
+    L.fa = o;     o = align_up(o + 4 * E, 16);
+    L.fb = o;     o = align_up(o + 4 * E, 16);
+    L.fQ = o;     o = align_up(o + 4 * E, 16);
+    L.ft = o;     o = align_up(o + 4 * E, 16);
+    L.beta = o;   o = align_up(o + 4 * E, 16);
+    L.vec = o;    o = align_up(o + 4 * 96, 16);
+    L.qk = o;     o = align_up(o + 4 * C, 16);
+    L.qa = o;     o = align_up(o + 4 * C, 16);
+    L.qb = o;     o = align_up(o + 4 * C, 16);
+    L.qlo = o;    o = align_up(o + 4 * C, 16);
+    L.qhi = o;    o = align_up(o + 4 * C, 16);
+    L.qD = o;     o = align_up(o + 8 * C, 16);
+    L.qg = o;     o = align_up(o + 8 * C * (uint32_t)M, 16);
+    L.order = o;  o = align_up(o + 4 * C, 16);
+    L.acc = o;    o = align_up(o + 4 * C, 16);
     if (accept_mode == 1) {
-        L.order = o;  o = align_up(o + 4 * (uint32_t)K, 16);
-        L.acc = o;    o = align_up(o + 4 * (uint32_t)K, 16);
-        L.bitmap = o; o = align_up(o + 4 * (uint32_t)((N + 31) / 32), 16);
+        L.bitmap = o;
+        o = align_up(o + 4 * (uint32_t)((N + 31) / 32), 16);
     } else {
-        L.order = L.acc = L.bitmap = o;
+        L.bitmap = o;
     }
     L.total = o;
     return L;
+}
+
+// Exchange area of a cooperative chain (caller-provided device memory): a header, then for each
+// of two step parities and each CTA, a count and up to kCoopMaxTop candidate records.
+struct CoopHeader {
+    unsigned long long arrive;  // grid barrier: arrivals so far
+    int32_t stop;               // set by CTA 0 before arriving when the time budget is spent
+    int32_t error;              // a barrier wait ran out
+    int32_t pad[12];
+};
+
+struct CoopRecord {
+    double D;        // key: exact, or a point inside [lo, hi]
+    float lo, hi;    // bounds on the key from the FP32 estimate
+    uint32_t k, a, b;
+    int32_t pad;
+    uint64_t g[5];   // per-shell swap vectors (biased bytes)
+};
+
+// Byte offsets inside the exchange area of a chain of `ctas` CTAs.
+__host__ __device__ inline size_t coop_counts_offset() { return sizeof(CoopHeader); }
+__host__ __device__ inline size_t coop_records_offset(int ctas) {
+    return (coop_counts_offset() + 2 * sizeof(int32_t) * (size_t)ctas + 63) / 64 * 64;
+}
+__host__ __device__ inline size_t coop_workspace_bytes(int ctas) {
+    return coop_records_offset(ctas) + 2 * (size_t)ctas * kCoopMaxTop * sizeof(CoopRecord);
 }
 
 // Launchers implemented in the .cu files.
@@ -86,5 +123,9 @@ cudaError_t launch_search_fcc(const ChainDesc& d, cudaStream_t stream);
 cudaError_t launch_search_bcc(const ChainDesc& d, cudaStream_t stream);
 cudaError_t launch_search_batch_fcc(const ChainDesc* descs_dev, int n, uint32_t smem_max, cudaStream_t stream);
 cudaError_t launch_search_batch_bcc(const ChainDesc* descs_dev, int n, uint32_t smem_max, cudaStream_t stream);
+cudaError_t launch_search_coop_fcc(const ChainDesc& d, cudaStream_t stream);
+cudaError_t launch_search_coop_bcc(const ChainDesc& d, cudaStream_t stream);
+int coop_max_ctas_fcc(const ChainDesc& d);
+int coop_max_ctas_bcc(const ChainDesc& d);
 
 }  // namespace hea

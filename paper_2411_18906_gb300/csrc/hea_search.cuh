@@ -1,17 +1,23 @@
-// hea_search.cuh -- swap scoring (Sec. 4.5, Sec. 4.6.2) and the persistent parallel Monte Carlo
-// search (Alg. parallel_mc; Sec. 4.6.3 selection; Sec. 4.6.4 convergence) for sm_103a.
+// hea_search.cuh -- swap scoring (Sec. 4.5, Sec. 4.6.2) and the parallel Monte Carlo search
+// (Alg. parallel_mc; Sec. 4.6.3 selection; Sec. 4.6.4 convergence) for sm_103a.
 //
-// One CTA runs one chain.  The cell's species live in shared memory (8 or 4 bits per site), the
-// counts and the per-entry objective coefficients next to them.  A step:
+// A chain's cell lives in shared memory (8 or 4 bits per site) next to its counts and the
+// per-entry objective coefficients.  A step:
 //   1. every thread draws candidates (Philox), builds the per-shell neighbour histograms of both
-//      sites (neighbours computed from coordinates), and evaluates an FP32 estimate of the swap
-//      key with a rigorous error bound;
-//   2. only candidates whose bound admits acceptance get the exact FP64 key (the same FMA chain
-//      as the reference definition), so every decision is taken on the exact key;
-//   3. best-of-K: block argmin over (D, k); multi-accept: eligible candidates are ranked by (D, k)
-//      and walked by one warp with a neighbourhood bitmap and an exact re-check against the
-//      running counts;
+//      sites (neighbours computed from coordinates) and the swap vector g = h_b - h_a, and
+//      evaluates an FP32 estimate of the swap key with a rigorous interval [lo, hi] around the
+//      exact binary64 key;
+//   2. decisions the intervals settle are taken on them; the exact binary64 key (the same FMA
+//      chain as the reference definition) is computed only where an interval straddles the
+//      acceptance threshold or overlaps another contender's interval, so every decision equals
+//      the one the exact keys give;
+//   3. best-of-K: argmin over (D, k); multi-accept: eligible candidates ranked by (D, k) and walked
+//      by one warp with a neighbourhood bitmap and a re-check against the running counts;
 //   4. the accepted swap(s) update species, counts and coefficients in place.
+// One CTA runs a chain (run_chain), or a grid of CTAs cooperates on one chain (run_coop_chain):
+// each CTA scores a slice of the K candidates, the CTAs exchange their best candidates through
+// global memory behind a grid barrier, and every CTA applies the same accepted swaps to its own
+// copy of the cell.
 #pragma once
 #include <cstdint>
 #include <cuda_runtime.h>
@@ -24,12 +30,13 @@ namespace hea {
 
 static __constant__ ShellTable c_shells[2] = {build_shell_table(kFCC), build_shell_table(kBCC)};
 
-// Error factor of the FP32 key estimate (see the bound in score_float) and its absolute floor.
+// Error factor of the FP32 key estimate (see score_float) and its absolute floor.
 constexpr float kRelBound = 1.220703125e-4f;   // 2^-13
 constexpr float kAbsBound = 7.52316385e-37f;   // 2^-120
+constexpr float kBetaScale = 3.814697265625e-06f;  // 2^-18
 
 struct ChainShared {
-    int qn;          // queue length (candidates that need the exact key)
+    int qn;          // queued candidates
     int n_elig;      // multi-accept: eligible candidates
     int n_acc;       // swaps accepted this step
     int stop;
@@ -37,9 +44,9 @@ struct ChainShared {
     int use_filter;
     int depth;
     int status;
-    float umin;      // best-of-K: min over candidates of the upper bound on D
-    int win_q;       // best-of-K: queue slot of the winner (-1 none)
-    double win_D;
+    int win_q;       // best-of-K: slot of the winner (-1 none)
+    int sync_ok;
+    float umin;      // min over candidates of the upper bound on D
     int64_t steps;
     int64_t accepted;
     uint64_t t0;
@@ -49,17 +56,24 @@ struct ChainShared {
     int red_q[32];
 };
 
-// Delta of entry (k,i,j) for a swap of species A (site a) and B (site b) with per-shell
-// histograms ha, hb (Sec. 4.5): g = h_b - h_a,
+// Per-shell swap vector g = h_b - h_a (Sec. 4.5), packed as one biased byte per species:
+// byte y holds 64 + h_b[y] - h_a[y] (every histogram byte is <= 24, so no borrow crosses bytes).
+constexpr uint64_t kGBias = 0x4040404040404040ull;
+
+__device__ __forceinline__ uint64_t pack_g(uint64_t ha, uint64_t hb) { return (hb + kGBias) - ha; }
+
+__device__ __forceinline__ int g_of(uint64_t gb, int y) { return (int)((gb >> (8 * y)) & 0xFFu) - 64; }
+
+// Delta of entry (k,i,j) for a swap of species A (site a) and B (site b):
 //   dN_ij = [i==A] g_j - [i==B] g_j + [j==A] g_i - [j==B] g_i.
-__device__ __forceinline__ int entry_delta(uint64_t ha, uint64_t hb, int A, int B, int i, int j) {
+__device__ __forceinline__ int entry_delta(uint64_t gb, int A, int B, int i, int j) {
     int d = 0;
     if (i == A || i == B) {
-        const int gj = hist_field(hb, j) - hist_field(ha, j);
+        const int gj = g_of(gb, j);
         d += (i == A) ? gj : -gj;
     }
     if (j == A || j == B) {
-        const int gi = hist_field(hb, i) - hist_field(ha, i);
+        const int gi = g_of(gb, i);
         d += (j == A) ? gi : -gi;
     }
     return d;
@@ -68,15 +82,15 @@ __device__ __forceinline__ int entry_delta(uint64_t ha, uint64_t hb, int A, int 
 // Exact key: change of F^2, D <- fma(dN, fma(a, dN, b), D) over (k,i,j) row-major; entries with
 // dN = 0 leave D unchanged bit for bit and are skipped.
 static __device__ double exact_key(int M, int S, const double* __restrict__ ca, const double* __restrict__ cb, int A,
-                            int B, const uint64_t* ha, const uint64_t* hb) {
+                                   int B, const uint64_t* gb) {
     double D = 0.0;
     for (int k = 0; k < M; ++k) {
-        const uint64_t a_h = ha[k], b_h = hb[k];
+        const uint64_t g_k = gb[k];
         for (int i = 0; i < S; ++i) {
             const bool row = (i == A || i == B);
             for (int j = 0; j < S; ++j) {
                 if (!row && j != A && j != B) continue;
-                const int d = entry_delta(a_h, b_h, A, B, i, j);
+                const int d = entry_delta(g_k, A, B, i, j);
                 if (d == 0) continue;
                 const int e = (k * S + i) * S + j;
                 const double x = (double)d;
@@ -87,24 +101,47 @@ static __device__ double exact_key(int M, int S, const double* __restrict__ ca, 
     return D;
 }
 
-// FP32 estimate of the key and a bound on its distance to the exact FP64 key.  Both evaluate
-// sum_e d_e (a_e d_e + b_e) from the same binary64 coefficients; the FP32 one from their float
+// Exact key against the running counts: coefficients recomputed in binary64 from cnt with the
+// arithmetic of the step-start coefficients.
+static __device__ double exact_key_running(int M, int S, const int32_t* cnt, const double* Q, const double* tgt,
+                                           const double* ca, const double* w, int A, int B, const uint64_t* gb) {
+    double D = 0.0;
+    for (int k = 0; k < M; ++k) {
+        const uint64_t g_k = gb[k];
+        for (int i = 0; i < S; ++i) {
+            const bool row = (i == A || i == B);
+            for (int j = 0; j < S; ++j) {
+                if (!row && j != A && j != B) continue;
+                const int dl = entry_delta(g_k, A, B, i, j);
+                if (dl == 0) continue;
+                const int e = (k * S + i) * S + j;
+                const double err = __dsub_rn(__dsub_rn(1.0, __dmul_rn((double)cnt[e], Q[e])), tgt[e]);
+                const double b = __dmul_rn(-2.0, __dmul_rn(w[k], __dmul_rn(Q[e], err)));
+                const double x = (double)dl;
+                D = __fma_rn(x, __fma_rn(ca[e], x, b), D);
+            }
+        }
+    }
+    return D;
+}
+
+// FP32 estimate of the key and a bound on its distance to the exact binary64 key.  Both evaluate
+// sum_e d_e (a_e d_e + b_e) from the same binary64 coefficients, the FP32 one from their float
 // roundings.  With n <= 320 nonzero entries the float evaluation is within
-// (n + 2) 2^-24 sum |d| (|a| |d| + |b|) (+ subnormal floor) of the real value and the FP64 chain
-// within (n + 1) 2^-53 of the same sum, so |D32 - D64| < 2^-13 sum |d|(|a||d| + |b|) + 2^-120.
+// (n + 2) 2^-24 sum |d| (|a| |d| + |b|) (+ a subnormal floor) of the real value and the binary64
+// chain within (n + 1) 2^-53 of it, so |D32 - D64| < 2^-13 sum |d| (|a| |d| + |b|) + 2^-120.
 __device__ __forceinline__ void score_float(int M, int S, const float* __restrict__ fa, const float* __restrict__ fb,
-                                            int A, int B, const uint64_t* ha, const uint64_t* hb, float& D,
-                                            float& err) {
+                                            int A, int B, const uint64_t* gb, float& D, float& err) {
     float acc = 0.f, mag = 0.f;
 #pragma unroll
     for (int k = 0; k < kMaxShells; ++k) {
         if (k >= M) break;
-        const uint64_t a_h = ha[k], b_h = hb[k];
+        const uint64_t g_k = gb[k];
         const int base = k * S * S;
-        const int gA = hist_field(b_h, A) - hist_field(a_h, A);
-        const int gB = hist_field(b_h, B) - hist_field(a_h, B);
+        const int gA = g_of(g_k, A);
+        const int gB = g_of(g_k, B);
         for (int y = 0; y < S; ++y) {
-            const int gy = hist_field(b_h, y) - hist_field(a_h, y);
+            const int gy = g_of(g_k, y);
             // Row A: dN_Ay = g_y + [y==A] g_A - [y==B] g_A; row B: dN_By = -g_y + [y==A] g_B - [y==B] g_B.
             const int dA = gy + (y == A ? gA : 0) - (y == B ? gA : 0);
             const int dB = -gy + (y == A ? gB : 0) - (y == B ? gB : 0);
@@ -141,25 +178,40 @@ __device__ __forceinline__ bool eligible(double D, bool null_move, double thresh
     return threshold > 0.0 && D <= threshold;
 }
 
-// Updates entry e after its count changed by d: e = (1 - n Q) - t; b = -2 (w (Q e)).
-__device__ __forceinline__ void refresh_entry(int e, int d, double w, int32_t* cnt, const double* Q,
-                                              const double* tgt, double* cb, float* fb) {
-    const int n = cnt[e] + d;
-    cnt[e] = n;
-    if (d == 0) return;
-    const double err = __dsub_rn(__dsub_rn(1.0, __dmul_rn((double)n, Q[e])), tgt[e]);
-    const double b = __dmul_rn(-2.0, __dmul_rn(w, __dmul_rn(Q[e], err)));
-    cb[e] = b;
-    fb[e] = (float)b;
+// Eligibility from an interval around the key: 1 eligible, 0 not, -1 undecided.
+__device__ __forceinline__ int eligible_interval(float lo, float hi, double threshold) {
+    if (threshold > 0.0) return ((double)hi <= threshold) ? 1 : (((double)lo > threshold) ? 0 : -1);
+    return (hi < 0.f) ? 1 : ((lo >= 0.f) ? 0 : -1);
 }
 
-// Site index of site + shell vector v (runtime v), for the bitmap of the multi-accept walk.
+// Bound beta_e on the distance between an FP32 coefficient b of entry e and the exact one: the FP32
+// evaluation of e = (1 - n Q) - t and b = -2 (w (Q e)) is within 8 * 2^-24 * 2 w Q (1 + |n Q| + |t| + |e|)
+// of the real values and the binary64 coefficient within 2^-50 of the same scale;
+// beta_e = 2^-18 * 2 w Q (1 + |n Q| + |t| + |e|).
+__device__ __forceinline__ float beta_of(float w, float Q, float nq, float t, float err) {
+    return kBetaScale * (2.0f * w * Q) * (1.0f + fabsf(nq) + fabsf(t) + fabsf(err));
+}
+
+// Running FP32 coefficient of entry e for count n during the multi-accept walk, and its bound.
+__device__ __forceinline__ void float_coefficient(int e, int n, float w, const float* fQ, const float* ft,
+                                                  float* fb, float* beta) {
+    const float nq = (float)n * fQ[e];
+    const float err = (1.0f - nq) - ft[e];
+    fb[e] = -2.0f * (w * (fQ[e] * err));
+    beta[e] = beta_of(w, fQ[e], nq, ft[e], err);
+}
+
+__device__ __forceinline__ bool better(double D1, uint32_t k1, double D2, uint32_t k2) {
+    return D1 < D2 || (D1 == D2 && k1 < k2);
+}
+
+// Site index of the point at half-unit position (X, Y, Z) + the shell vector packed in `pv`
+// (signed bytes dx, dy, dz).
+__device__ __forceinline__ int unpack_comp(uint32_t pv, int c) { return (int)(int8_t)((pv >> (8 * c)) & 0xFFu); }
+
 template <int KIND>
-__device__ __forceinline__ uint32_t neighbour_of(const Geo& g, uint32_t site, int v) {
-    int X, Y, Z;
-    site_coords<KIND>(g, site, X, Y, Z);
-    const ShellTable& T = c_shells[KIND];
-    int x = X + T.v[v][0], y = Y + T.v[v][1], z = Z + T.v[v][2];
+__device__ __forceinline__ uint32_t neighbour_at(const Geo& g, int X, int Y, int Z, uint32_t pv) {
+    int x = X + unpack_comp(pv, 0), y = Y + unpack_comp(pv, 1), z = Z + unpack_comp(pv, 2);
     const int PX = 2 * g.Lx, PY = 2 * g.Ly, PZ = 2 * g.Lz;
     x += (x < 0) ? PX : 0;
     x -= (x >= PX) ? PX : 0;
@@ -171,51 +223,89 @@ __device__ __forceinline__ uint32_t neighbour_of(const Geo& g, uint32_t site, in
     return (uint32_t)(b * g.V + (z >> 1) * g.LxLy + (y >> 1) * g.Lx + (x >> 1));
 }
 
-__device__ __forceinline__ bool better(double D1, uint32_t k1, double D2, uint32_t k2) {
-    return D1 < D2 || (D1 == D2 && k1 < k2);
+// Sets (or clears) the bits of the closed shell neighbourhood of `site` in the walk bitmap; the
+// calling lanes split the Z_tot + 1 sites between them.  `vec` is the shell-vector table in
+// shared memory.
+template <int KIND, bool SET>
+__device__ __forceinline__ void mark_neighbourhood(const Geo& g, uint32_t site, int ztot, int lane, int lanes,
+                                                   const uint32_t* vec, uint32_t* bitmap) {
+    int X, Y, Z;
+    site_coords<KIND>(g, site, X, Y, Z);
+    for (int v = lane; v <= ztot; v += lanes) {
+        const uint32_t s = (v == 0) ? site : neighbour_at<KIND>(g, X, Y, Z, vec[v - 1]);
+        if (SET)
+            atomicOr(&bitmap[s >> 5], 1u << (s & 31));
+        else
+            atomicAnd(&bitmap[s >> 5], ~(1u << (s & 31)));
+    }
 }
 
-// ------------------------------------------------------------------------------------------------
-// One chain, run to completion by the calling CTA.
-// ------------------------------------------------------------------------------------------------
-template <int KIND, int BITS>
-__device__ void run_chain(const ChainDesc& d, uint8_t* smem, ChainShared& sh) {
-    constexpr int MX = kMaxShells;
-    const int M = d.M, S = d.S, E = M * S * S, K = d.K;
-    const int tid = threadIdx.x, T = blockDim.x, lane = tid & 31, warp = tid >> 5, nwarps = T >> 5;
-    const ChainLayout L = chain_layout(d.N, M, S, K, BITS, d.accept_mode);
-    uint8_t* s_types = smem + L.types;
-    int32_t* s_cnt = reinterpret_cast<int32_t*>(smem + L.cnt);
-    double* s_Q = reinterpret_cast<double*>(smem + L.Q);
-    double* s_t = reinterpret_cast<double*>(smem + L.tgt);
-    double* s_ca = reinterpret_cast<double*>(smem + L.ca);
-    double* s_cb = reinterpret_cast<double*>(smem + L.cb);
-    float* s_fa = reinterpret_cast<float*>(smem + L.fa);
-    float* s_fb = reinterpret_cast<float*>(smem + L.fb);
-    uint32_t* s_qk = reinterpret_cast<uint32_t*>(smem + L.qk);
-    uint32_t* s_qa = reinterpret_cast<uint32_t*>(smem + L.qa);
-    uint32_t* s_qb = reinterpret_cast<uint32_t*>(smem + L.qb);
-    float* s_qlo = reinterpret_cast<float*>(smem + L.qlo);
-    double* s_qD = reinterpret_cast<double*>(smem + L.qD);
-    uint64_t* s_qha = reinterpret_cast<uint64_t*>(smem + L.qha);
-    uint64_t* s_qhb = reinterpret_cast<uint64_t*>(smem + L.qhb);
-    uint32_t* s_order = reinterpret_cast<uint32_t*>(smem + L.order);
-    uint32_t* s_acc = reinterpret_cast<uint32_t*>(smem + L.acc);
-    uint32_t* s_bitmap = reinterpret_cast<uint32_t*>(smem + L.bitmap);
+// Pointers into a chain's shared memory.
+struct ChainSmem {
+    uint8_t* types;
+    int32_t* cnt;
+    double *Q, *tgt, *ca, *cb;
+    float *fa, *fb, *fQ, *ft, *beta;
+    uint32_t* vec;
+    uint32_t *qk, *qa, *qb;
+    float *qlo, *qhi;
+    double* qD;
+    uint64_t* qg;
+    uint32_t *order, *acc, *bitmap;
 
+    __device__ ChainSmem(uint8_t* smem, const ChainLayout& L) {
+        types = smem + L.types;
+        cnt = reinterpret_cast<int32_t*>(smem + L.cnt);
+        Q = reinterpret_cast<double*>(smem + L.Q);
+        tgt = reinterpret_cast<double*>(smem + L.tgt);
+        ca = reinterpret_cast<double*>(smem + L.ca);
+        cb = reinterpret_cast<double*>(smem + L.cb);
+        fa = reinterpret_cast<float*>(smem + L.fa);
+        fb = reinterpret_cast<float*>(smem + L.fb);
+        fQ = reinterpret_cast<float*>(smem + L.fQ);
+        ft = reinterpret_cast<float*>(smem + L.ft);
+        beta = reinterpret_cast<float*>(smem + L.beta);
+        vec = reinterpret_cast<uint32_t*>(smem + L.vec);
+        qk = reinterpret_cast<uint32_t*>(smem + L.qk);
+        qa = reinterpret_cast<uint32_t*>(smem + L.qa);
+        qb = reinterpret_cast<uint32_t*>(smem + L.qb);
+        qlo = reinterpret_cast<float*>(smem + L.qlo);
+        qhi = reinterpret_cast<float*>(smem + L.qhi);
+        qD = reinterpret_cast<double*>(smem + L.qD);
+        qg = reinterpret_cast<uint64_t*>(smem + L.qg);
+        order = reinterpret_cast<uint32_t*>(smem + L.order);
+        acc = reinterpret_cast<uint32_t*>(smem + L.acc);
+        bitmap = reinterpret_cast<uint32_t*>(smem + L.bitmap);
+    }
+};
+
+// Per-chain constants derived from the descriptor.
+struct ChainCtx {
     Geo g;
-    g.Lx = d.Lx;
-    g.Ly = d.Ly;
-    g.Lz = d.Lz;
-    g.V = d.Lx * d.Ly * d.Lz;
-    g.LxLy = d.Lx * d.Ly;
-    g.N = d.N;
-    const uint32_t N = (uint32_t)d.N;
-    const double thr = d.threshold;
-    const uint32_t seed_lo = (uint32_t)(d.seed & 0xFFFFFFFFu), seed_hi = (uint32_t)(d.seed >> 32);
-    const ShellTable& TAB = c_shells[KIND];
-    const int ztot = TAB.first[M];
+    int M, S, E, K, ztot;
+    uint32_t N;
+    double thr;
+    uint32_t seed_lo, seed_hi;
+    bool use_filter;
+};
 
+// ---- set-up: species (validated against S), counts, coefficients, shell vectors ----------------
+template <int KIND, int BITS>
+__device__ void chain_setup(const ChainDesc& d, ChainSmem& m, ChainShared& sh, ChainCtx& c) {
+    const int tid = threadIdx.x, T = blockDim.x;
+    c.g = make_geo(KIND, d.Lx, d.Ly, d.Lz);
+    c.M = d.M;
+    c.S = d.S;
+    c.E = d.M * d.S * d.S;
+    c.K = d.K;
+    c.N = (uint32_t)d.N;
+    c.thr = d.threshold;
+    c.seed_lo = (uint32_t)(d.seed & 0xFFFFFFFFu);
+    c.seed_hi = (uint32_t)(d.seed >> 32);
+    const ShellTable& TAB = c_shells[KIND];
+    c.ztot = TAB.first[c.M];
+    const int S = c.S, E = c.E;
+    const uint32_t N = c.N;
     if (tid == 0) {
         sh.bad = 0;
         sh.use_filter = 1;
@@ -227,22 +317,23 @@ __device__ void run_chain(const ChainDesc& d, uint8_t* smem, ChainShared& sh) {
         sh.t0 = globaltimer_ns();
     }
     __syncthreads();
-
-    // ---- load species (validated against S) and counts; objective coefficients ----
     if (BITS == 8) {
         for (uint32_t i = tid; i < N; i += T) {
             const uint8_t v = d.types[i];
             if (v >= S) sh.bad = 1;
-            s_types[i] = v;
+            m.types[i] = v;
         }
     } else {
         for (uint32_t i = tid; i < (N + 1) / 2; i += T) {
             const uint8_t v0 = d.types[2 * i];
             const uint8_t v1 = (2 * i + 1 < N) ? d.types[2 * i + 1] : 0;
             if (v0 >= S || v1 >= S) sh.bad = 1;
-            s_types[i] = (uint8_t)((v0 & 0xF) | ((v1 & 0xF) << 4));
+            m.types[i] = (uint8_t)((v0 & 0xF) | ((v1 & 0xF) << 4));
         }
     }
+    for (int v = tid; v < c.ztot; v += T)
+        m.vec[v] = (uint32_t)(uint8_t)TAB.v[v][0] | ((uint32_t)(uint8_t)TAB.v[v][1] << 8) |
+                   ((uint32_t)(uint8_t)TAB.v[v][2] << 16);
     for (int e = tid; e < E; e += T) {
         const int k = e / (S * S), i = (e / S) % S, j = e % S;
         const double w = d.w[k];
@@ -253,13 +344,17 @@ __device__ void run_chain(const ChainDesc& d, uint8_t* smem, ChainShared& sh) {
         const double err = __dsub_rn(__dsub_rn(1.0, __dmul_rn((double)n, Q)), t);
         const double a = __dmul_rn(w, __dmul_rn(Q, Q));
         const double b = __dmul_rn(-2.0, __dmul_rn(w, __dmul_rn(Q, err)));
-        s_cnt[e] = n;
-        s_Q[e] = Q;
-        s_t[e] = t;
-        s_ca[e] = a;
-        s_cb[e] = b;
-        s_fa[e] = (float)a;
-        s_fb[e] = (float)b;
+        m.cnt[e] = n;
+        m.Q[e] = Q;
+        m.tgt[e] = t;
+        m.ca[e] = a;
+        m.cb[e] = b;
+        m.fa[e] = (float)a;
+        m.fb[e] = (float)b;
+        m.fQ[e] = (float)Q;
+        m.ft[e] = (float)t;
+        const float nq = (float)n * (float)Q;
+        m.beta[e] = beta_of((float)w, (float)Q, nq, (float)t, (1.0f - nq) - (float)t);
         // The FP32 estimate needs every |a| dN^2 and |b| dN to stay far inside the float range;
         // |e| <= 1 + N / N_j + |t| bounds b over the whole search.
         const double zz = 2.0 * TAB.z[k];
@@ -267,273 +362,372 @@ __device__ void run_chain(const ChainDesc& d, uint8_t* smem, ChainShared& sh) {
         if (!(a * zz * zz < 1e30) || !(bmax * zz < 1e30)) sh.use_filter = 0;
     }
     if (d.accept_mode == 1)
-        for (uint32_t i = tid; i < (N + 31) / 32; i += T) s_bitmap[i] = 0;
+        for (uint32_t i = tid; i < (N + 31) / 32; i += T) m.bitmap[i] = 0;
     __syncthreads();
-    if (sh.bad) {
-        if (tid == 0) {
-            d.result->steps = 0;
-            d.result->trials = 0;
-            d.result->accepted = 0;
-            d.result->depth = d.depth0;
-            d.result->status = HEA_EINVAL;
-            d.result->f2 = CUDART_NAN;
-            d.result->f = CUDART_NAN;
+    c.use_filter = sh.use_filter != 0;
+}
+
+// ---- 1. score candidates k in [k_begin, k_end) of step `step`; queue the ones that may matter ----
+// Returns this thread's minimum of the upper bounds (null moves count as 0).
+template <int KIND, int BITS>
+__device__ float score_range(const ChainDesc& d, ChainSmem& m, ChainShared& sh, const ChainCtx& c, uint32_t step,
+                             uint32_t k_begin, uint32_t k_end) {
+    constexpr int MX = kMaxShells;
+    const int M = c.M;
+    auto onehot = [&](uint32_t n) -> uint64_t { return 1ull << (8 * load_species<BITS>(m.types, n)); };
+    float my_umin = CUDART_INF_F;
+    for (uint32_t kk = k_begin + threadIdx.x; kk < k_end; kk += blockDim.x) {
+        const Rand4 r = philox(kk, step, d.chain, 1u, c.seed_lo, c.seed_hi);
+        const uint32_t a = __umulhi(r.r0, c.N), b = __umulhi(r.r1, c.N);
+        const int A = load_species<BITS>(m.types, a), B = load_species<BITS>(m.types, b);
+        if (a == b || A == B) {
+            my_umin = fminf(my_umin, 0.f);
+            if (c.thr > 0.0) {
+                const int slot = atomicAdd(&sh.qn, 1);
+                m.qk[slot] = kk;
+                m.qa[slot] = a;
+                m.qb[slot] = b;
+                m.qlo[slot] = 0.f;
+                m.qhi[slot] = 0.f;
+                for (int k = 0; k < M; ++k) m.qg[slot * M + k] = kGBias;
+            }
+            continue;
         }
-        return;
+        uint64_t ha[MX], hb[MX], gb[MX];
+        neighbour_histogram_upto<KIND, MX>(c.g, a, b, onehot, ha, M);
+        neighbour_histogram_upto<KIND, MX>(c.g, b, a, onehot, hb, M);
+#pragma unroll
+        for (int k = 0; k < MX; ++k) gb[k] = pack_g(ha[k], hb[k]);
+        float lo = -CUDART_INF_F, hi = CUDART_INF_F;
+        if (c.use_filter) {
+            float Dt, err;
+            score_float(M, c.S, m.fa, m.fb, A, B, gb, Dt, err);
+            hi = __fadd_ru(Dt, err);
+            lo = __fadd_rd(Dt, -err);
+            my_umin = fminf(my_umin, hi);
+            if ((double)lo > c.thr) continue;   // cannot be accepted
+        }
+        const int slot = atomicAdd(&sh.qn, 1);
+        m.qk[slot] = kk;
+        m.qa[slot] = a;
+        m.qb[slot] = b;
+        m.qlo[slot] = lo;
+        m.qhi[slot] = hi;
+#pragma unroll
+        for (int k = 0; k < MX; ++k)
+            if (k < M) m.qg[slot * M + k] = gb[k];
     }
-    const bool use_filter = sh.use_filter != 0;
+    return my_umin;
+}
 
-    auto onehot = [&](uint32_t n) -> uint64_t { return 1ull << (8 * load_species<BITS>(s_types, n)); };
+__device__ __forceinline__ float block_min(float v, ChainShared& sh) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fminf(v, __shfl_xor_sync(0xFFFFFFFFu, v, o));
+    if (lane == 0) sh.red_f[warp] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float u = CUDART_INF_F;
+        for (int w = 0; w < nw; ++w) u = fminf(u, sh.red_f[w]);
+        sh.umin = u;
+    }
+    __syncthreads();
+    return sh.umin;
+}
 
-    // ---- step loop ----
-    while (!sh.stop) {
-        const uint32_t step = d.step0 + (uint32_t)sh.steps;
-        if (tid == 0) {
-            sh.qn = 0;
-            sh.n_elig = 0;
-            sh.n_acc = 0;
-            sh.win_q = -1;
+// ---- best-of-K: exact keys of the contenders, block argmin over (D, k) --------------------------
+// A contender is a queued candidate with lo <= min(umin, threshold): the argmin, whenever it is
+// acceptable, is one of them.  Sets sh.win_q to the best slot, or -1.
+template <int BITS>
+__device__ void best_of_queue(ChainSmem& m, ChainShared& sh, const ChainCtx& c, float umin) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const double tau = c.use_filter ? fmin((double)umin, c.thr) : CUDART_INF;
+    double bD = CUDART_INF;
+    uint32_t bk = 0xFFFFFFFFu;
+    int bq = -1;
+    const int qn = sh.qn;
+    for (int q = threadIdx.x; q < qn; q += blockDim.x) {
+        if (c.use_filter && (double)m.qlo[q] > tau) continue;
+        const uint32_t a = m.qa[q], b = m.qb[q];
+        const int A = load_species<BITS>(m.types, a), B = load_species<BITS>(m.types, b);
+        const double D = (a == b || A == B) ? 0.0 : exact_key(c.M, c.S, m.ca, m.cb, A, B, m.qg + q * c.M);
+        m.qD[q] = D;
+        if (better(D, m.qk[q], bD, bk)) {
+            bD = D;
+            bk = m.qk[q];
+            bq = q;
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const double oD = __shfl_xor_sync(0xFFFFFFFFu, bD, o);
+        const uint32_t ok = __shfl_xor_sync(0xFFFFFFFFu, bk, o);
+        const int oq = __shfl_xor_sync(0xFFFFFFFFu, bq, o);
+        if (better(oD, ok, bD, bk)) {
+            bD = oD;
+            bk = ok;
+            bq = oq;
+        }
+    }
+    if (lane == 0) {
+        sh.red_d[warp] = bD;
+        sh.red_k[warp] = bk;
+        sh.red_q[warp] = bq;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double D = CUDART_INF;
+        uint32_t k = 0xFFFFFFFFu;
+        int q = -1;
+        for (int w = 0; w < nw; ++w)
+            if (better(sh.red_d[w], sh.red_k[w], D, k)) {
+                D = sh.red_d[w];
+                k = sh.red_k[w];
+                q = sh.red_q[w];
+            }
+        sh.win_q = q;
+    }
+    __syncthreads();
+}
+
+// Applies the swap in slot q (known acceptable) to species, counts and coefficients.
+template <int BITS>
+__device__ void apply_slot(const ChainDesc& d, ChainSmem& m, ChainShared& sh, const ChainCtx& c, int q) {
+    const uint32_t a = m.qa[q], b = m.qb[q];
+    const int A = load_species<BITS>(m.types, a), B = load_species<BITS>(m.types, b);
+    const int S = c.S;
+    for (int e = threadIdx.x; e < c.E; e += blockDim.x) {
+        const int k = e / (S * S), i = (e / S) % S, j = e % S;
+        const int dl = entry_delta(m.qg[q * c.M + k], A, B, i, j);
+        if (dl == 0) continue;
+        const int n = m.cnt[e] + dl;
+        m.cnt[e] = n;
+        const double err = __dsub_rn(__dsub_rn(1.0, __dmul_rn((double)n, m.Q[e])), m.tgt[e]);
+        const double bcoef = __dmul_rn(-2.0, __dmul_rn(d.w[k], __dmul_rn(m.Q[e], err)));
+        m.cb[e] = bcoef;
+        m.fb[e] = (float)bcoef;
+        const float nq = (float)n * m.fQ[e];
+        m.beta[e] = beta_of((float)d.w[k], m.fQ[e], nq, m.ft[e], (1.0f - nq) - m.ft[e]);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        store_species<BITS>(m.types, a, B);
+        store_species<BITS>(m.types, b, A);
+        sh.n_acc = 1;
+    }
+}
+
+// ---- multi-accept: eligible candidates of slots [0, n) ranked by (D, k) into m.order ------------
+// Eligibility is decided on the interval where it can be and on the exact key otherwise; among the
+// eligible, a candidate gets its exact key when its interval overlaps another one's.  Ranking by
+// (exact key, or the interval midpoint; k) is then the ranking by (D, k): disjoint intervals order
+// their keys, overlapping ones are ordered by exact keys.  With group_top > 0 only the group_top
+// best of each group (k / group_size) stay.  Sets sh.n_elig.
+template <int BITS>
+__device__ void rank_eligible(ChainSmem& m, ChainShared& sh, const ChainCtx& c, int n, int group_size,
+                              int group_top) {
+    const int tid = threadIdx.x, T = blockDim.x;
+    if (tid == 0) sh.n_elig = 0;
+    __syncthreads();
+    for (int q = tid; q < n; q += T) {
+        const uint32_t a = m.qa[q], b = m.qb[q];
+        const int A = load_species<BITS>(m.types, a), B = load_species<BITS>(m.types, b);
+        if (a == b || A == B) continue;   // null moves are never accepted
+        int v = eligible_interval(m.qlo[q], m.qhi[q], c.thr);
+        bool exact = false;
+        if (v < 0) {
+            m.qD[q] = exact_key(c.M, c.S, m.ca, m.cb, A, B, m.qg + q * c.M);
+            v = eligible(m.qD[q], false, c.thr) ? 1 : 0;
+            exact = true;
+        }
+        if (v == 1) {
+            if (!exact) m.qD[q] = 0.5 * ((double)m.qlo[q] + (double)m.qhi[q]);
+            m.acc[atomicAdd(&sh.n_elig, 1)] = (uint32_t)q | (exact ? 0x80000000u : 0u);
+        }
+    }
+    __syncthreads();
+    const int ne = sh.n_elig;
+    for (int s = tid; s < ne; s += T) {
+        if (m.acc[s] & 0x80000000u) continue;
+        const uint32_t q = m.acc[s];
+        const float lo = m.qlo[q], hi = m.qhi[q];
+        bool overlap = false;
+        for (int o = 0; o < ne && !overlap; ++o) {
+            if (o == s) continue;
+            const uint32_t q2 = m.acc[o] & 0x7FFFFFFFu;
+            overlap = (lo <= m.qhi[q2]) && (m.qlo[q2] <= hi);
+        }
+        if (overlap) {
+            const int A = load_species<BITS>(m.types, m.qa[q]), B = load_species<BITS>(m.types, m.qb[q]);
+            m.qD[q] = exact_key(c.M, c.S, m.ca, m.cb, A, B, m.qg + q * c.M);
+        }
+    }
+    __syncthreads();
+    for (int s = tid; s < ne; s += T) m.acc[s] &= 0x7FFFFFFFu;
+    __syncthreads();
+    int keep = ne;
+    if (group_top > 0) {
+        const uint32_t G = (uint32_t)(group_size > 0 ? group_size : c.K);
+        for (int s = tid; s < ne; s += T) {
+            const uint32_t q = m.acc[s];
+            const uint32_t grp = m.qk[q] / G;
+            int ahead = 0;
+            for (int o = 0; o < ne; ++o) {
+                const uint32_t q2 = m.acc[o];
+                if (m.qk[q2] / G == grp && better(m.qD[q2], m.qk[q2], m.qD[q], m.qk[q])) ++ahead;
+            }
+            m.order[s] = (ahead < group_top) ? q : 0xFFFFFFFFu;
         }
         __syncthreads();
-
-        // 1. Score every candidate with the FP32 estimate; queue those that may be accepted.
-        float my_umin = CUDART_INF_F;
-        for (int kk = tid; kk < K; kk += T) {
-            const Rand4 r = philox((uint32_t)kk, step, d.chain, 1u, seed_lo, seed_hi);
-            const uint32_t a = __umulhi(r.r0, N), b = __umulhi(r.r1, N);
-            const int A = load_species<BITS>(s_types, a), B = load_species<BITS>(s_types, b);
-            if (a == b || A == B) {
-                my_umin = fminf(my_umin, 0.f);
-                if (thr > 0.0) {
-                    const int slot = atomicAdd(&sh.qn, 1);
-                    s_qk[slot] = (uint32_t)kk;
-                    s_qa[slot] = a;
-                    s_qb[slot] = b;
-                    s_qlo[slot] = 0.f;
-                }
-                continue;
-            }
-            uint64_t ha[MX], hb[MX];
-            neighbour_histogram_upto<KIND, MX>(g, a, b, onehot, ha, M);
-            neighbour_histogram_upto<KIND, MX>(g, b, a, onehot, hb, M);
-            float lo = -CUDART_INF_F;
-            if (use_filter) {
-                float Dt, err;
-                score_float(M, S, s_fa, s_fb, A, B, ha, hb, Dt, err);
-                my_umin = fminf(my_umin, __fadd_ru(Dt, err));
-                lo = __fadd_rd(Dt, -err);
-                if ((double)lo > thr) continue;
-            }
-            const int slot = atomicAdd(&sh.qn, 1);
-            s_qk[slot] = (uint32_t)kk;
-            s_qa[slot] = a;
-            s_qb[slot] = b;
-            s_qlo[slot] = lo;
-#pragma unroll
-            for (int k = 0; k < MX; ++k) {
-                if (k < M) {
-                    s_qha[slot * M + k] = ha[k];
-                    s_qhb[slot * M + k] = hb[k];
-                }
-            }
+        if (tid == 0) sh.n_elig = 0;
+        __syncthreads();
+        for (int s = tid; s < ne; s += T)
+            if (m.order[s] != 0xFFFFFFFFu) m.acc[atomicAdd(&sh.n_elig, 1)] = m.order[s];
+        __syncthreads();
+        keep = sh.n_elig;
+    }
+    for (int s = tid; s < keep; s += T) {
+        const uint32_t q = m.acc[s];
+        int rank = 0;
+        for (int o = 0; o < keep; ++o) {
+            const uint32_t q2 = m.acc[o];
+            rank += better(m.qD[q2], m.qk[q2], m.qD[q], m.qk[q]) ? 1 : 0;
         }
+        m.order[rank] = q;
+    }
+    __syncthreads();
+}
 
-        if (d.accept_mode == 0) {
-            // 2a. Block minimum of the upper bounds.
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) my_umin = fminf(my_umin, __shfl_xor_sync(0xFFFFFFFFu, my_umin, o));
-            if (lane == 0) sh.red_f[warp] = my_umin;
-            __syncthreads();
-            if (tid == 0) {
-                float u = CUDART_INF_F;
-                for (int w = 0; w < nwarps; ++w) u = fminf(u, sh.red_f[w]);
-                sh.umin = u;
-            }
-            __syncthreads();
-            // 3a. Exact keys for candidates that can still be the accepted argmin.
-            const double tau = use_filter ? fmin((double)sh.umin, thr) : CUDART_INF;
-            double bD = CUDART_INF;
-            uint32_t bk = 0xFFFFFFFFu;
-            int bq = -1;
-            const int qn = sh.qn;
-            for (int q = tid; q < qn; q += T) {
-                if (use_filter && (double)s_qlo[q] > tau) continue;
-                const uint32_t a = s_qa[q], b = s_qb[q];
-                const int A = load_species<BITS>(s_types, a), B = load_species<BITS>(s_types, b);
-                const double D = (a == b || A == B) ? 0.0 : exact_key(M, S, s_ca, s_cb, A, B, s_qha + q * M, s_qhb + q * M);
-                if (better(D, s_qk[q], bD, bk)) {
-                    bD = D;
-                    bk = s_qk[q];
-                    bq = q;
-                }
-            }
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                const double oD = __shfl_xor_sync(0xFFFFFFFFu, bD, o);
-                const uint32_t ok = __shfl_xor_sync(0xFFFFFFFFu, bk, o);
-                const int oq = __shfl_xor_sync(0xFFFFFFFFu, bq, o);
-                if (better(oD, ok, bD, bk)) {
-                    bD = oD;
-                    bk = ok;
-                    bq = oq;
-                }
-            }
-            if (lane == 0) {
-                sh.red_d[warp] = bD;
-                sh.red_k[warp] = bk;
-                sh.red_q[warp] = bq;
-            }
-            __syncthreads();
-            if (tid == 0) {
-                double D = CUDART_INF;
-                uint32_t k = 0xFFFFFFFFu;
-                int q = -1;
-                for (int w = 0; w < nwarps; ++w)
-                    if (better(sh.red_d[w], sh.red_k[w], D, k)) {
-                        D = sh.red_d[w];
-                        k = sh.red_k[w];
-                        q = sh.red_q[w];
-                    }
-                bool take = false;
-                if (q >= 0) {
-                    const uint32_t a = s_qa[q], b = s_qb[q];
-                    const bool null_move = (a == b) || load_species<BITS>(s_types, a) == load_species<BITS>(s_types, b);
-                    take = eligible(D, null_move, thr);
-                }
-                sh.win_q = take ? q : -1;
-                sh.win_D = D;
-            }
-            __syncthreads();
-            // 4a. Apply the winner.
-            const int q = sh.win_q;
-            if (q >= 0) {
-                const uint32_t a = s_qa[q], b = s_qb[q];
-                const int A = load_species<BITS>(s_types, a), B = load_species<BITS>(s_types, b);
-                for (int e = tid; e < E; e += T) {
+// ---- multi-accept walk over m.order[0, ne) by warp 0 (sequential by definition) ----------------
+// Each re-check against the running counts is an FP32 estimate over the lanes with a rigorous
+// bound; the exact binary64 key is computed only when the bound cannot decide eligibility.
+template <int KIND, int BITS>
+__device__ void walk(const ChainDesc& d, ChainSmem& m, ChainShared& sh, const ChainCtx& c, int ne) {
+    const int lane = threadIdx.x & 31;
+    if ((threadIdx.x >> 5) == 0) {
+        const int S = c.S, M = c.M, E = c.E;
+        int n_acc = 0;
+        for (int r = 0; r < ne; ++r) {
+            if (d.max_accept > 0 && n_acc >= d.max_accept) break;
+            const uint32_t q = m.order[r];
+            const uint32_t a = m.qa[q], b = m.qb[q];
+            const bool blocked = ((m.bitmap[a >> 5] >> (a & 31)) & 1u) | ((m.bitmap[b >> 5] >> (b & 31)) & 1u);
+            if (blocked) continue;
+            const int A = load_species<BITS>(m.types, a), B = load_species<BITS>(m.types, b);
+            const uint64_t* gq = m.qg + q * M;
+            bool take = true;   // before the first accept the running state is the step-start state
+            if (n_acc > 0) {
+                float acc = 0.f, mag = 0.f, bet = 0.f;
+                for (int e = lane; e < E; e += 32) {
                     const int k = e / (S * S), i = (e / S) % S, j = e % S;
-                    const int dl = entry_delta(s_qha[q * M + k], s_qhb[q * M + k], A, B, i, j);
-                    refresh_entry(e, dl, d.w[k], s_cnt, s_Q, s_t, s_cb, s_fb);
+                    const int dl = entry_delta(gq[k], A, B, i, j);
+                    if (dl == 0) continue;
+                    const float x = (float)dl, ax = fabsf(x);
+                    acc = fmaf(x, fmaf(m.fa[e], x, m.fb[e]), acc);
+                    mag = fmaf(ax, fmaf(fabsf(m.fa[e]), ax, fabsf(m.fb[e])), mag);
+                    bet = fmaf(ax, m.beta[e], bet);
                 }
-                __syncthreads();
-                if (tid == 0) {
-                    store_species<BITS>(s_types, a, B);
-                    store_species<BITS>(s_types, b, A);
-                    sh.n_acc = 1;
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    acc += __shfl_xor_sync(0xFFFFFFFFu, acc, o);
+                    mag += __shfl_xor_sync(0xFFFFFFFFu, mag, o);
+                    bet += __shfl_xor_sync(0xFFFFFFFFu, bet, o);
                 }
-            }
-        } else {
-            __syncthreads();
-            // 2b. Exact keys of all queued candidates; collect the eligible ones.
-            const int qn = sh.qn;
-            for (int q = tid; q < qn; q += T) {
-                const uint32_t a = s_qa[q], b = s_qb[q];
-                const int A = load_species<BITS>(s_types, a), B = load_species<BITS>(s_types, b);
-                const bool null_move = (a == b || A == B);
-                const double D = null_move ? 0.0 : exact_key(M, S, s_ca, s_cb, A, B, s_qha + q * M, s_qhb + q * M);
-                s_qD[q] = D;
-                if (eligible(D, null_move, thr)) {
-                    const int slot = atomicAdd(&sh.n_elig, 1);
-                    s_acc[slot] = (uint32_t)q;
-                }
-            }
-            __syncthreads();
-            // 3b. Rank the eligible candidates by (D, k).
-            const int ne = sh.n_elig;
-            for (int s = tid; s < ne; s += T) {
-                const uint32_t q = s_acc[s];
-                const double D = s_qD[q];
-                const uint32_t k = s_qk[q];
-                int rank = 0;
-                for (int o = 0; o < ne; ++o) {
-                    const uint32_t q2 = s_acc[o];
-                    rank += better(s_qD[q2], s_qk[q2], D, k) ? 1 : 0;
-                }
-                s_order[rank] = q;
-            }
-            __syncthreads();
-            // 4b. One warp walks the ranked list (sequential by definition).
-            if (warp == 0) {
-                int n_acc = 0;
-                for (int r = 0; r < ne; ++r) {
-                    if (d.max_accept > 0 && n_acc >= d.max_accept) break;
-                    const uint32_t q = s_order[r];
-                    const uint32_t a = s_qa[q], b = s_qb[q];
-                    const bool blocked = ((s_bitmap[a >> 5] >> (a & 31)) & 1u) | ((s_bitmap[b >> 5] >> (b & 31)) & 1u);
-                    if (blocked) continue;
-                    const int A = load_species<BITS>(s_types, a), B = load_species<BITS>(s_types, b);
+                const float err = fmaf(mag, kRelBound, bet + kAbsBound);
+                int verdict = eligible_interval(__fadd_rd(acc, -err), __fadd_ru(acc, err), c.thr);
+                if (verdict < 0) {
                     double Dp = 0.0;
-                    if (lane == 0)
-                        Dp = (r == 0) ? s_qD[q] : exact_key(M, S, s_ca, s_cb, A, B, s_qha + q * M, s_qhb + q * M);
+                    if (lane == 0) Dp = exact_key_running(M, S, m.cnt, m.Q, m.tgt, m.ca, d.w, A, B, gq);
                     Dp = __shfl_sync(0xFFFFFFFFu, Dp, 0);
-                    if (!eligible(Dp, false, thr)) continue;
-                    for (int e = lane; e < E; e += 32) {
-                        const int k = e / (S * S), i = (e / S) % S, j = e % S;
-                        const int dl = entry_delta(s_qha[q * M + k], s_qhb[q * M + k], A, B, i, j);
-                        refresh_entry(e, dl, d.w[k], s_cnt, s_Q, s_t, s_cb, s_fb);
-                    }
-                    for (int v = lane; v < 2 * (ztot + 1); v += 32) {
-                        const uint32_t c = (v <= ztot) ? a : b;
-                        const int vv = (v <= ztot) ? v : v - (ztot + 1);
-                        const uint32_t site = (vv == 0) ? c : neighbour_of<KIND>(g, c, vv - 1);
-                        atomicOr(&s_bitmap[site >> 5], 1u << (site & 31));
-                    }
-                    if (lane == 0) {
-                        store_species<BITS>(s_types, a, B);
-                        store_species<BITS>(s_types, b, A);
-                        s_acc[n_acc] = q;
-                    }
-                    ++n_acc;
-                    __syncwarp();
+                    verdict = eligible(Dp, false, c.thr) ? 1 : 0;
                 }
-                if (lane == 0) sh.n_acc = n_acc;
+                take = verdict == 1;
             }
-            __syncthreads();
-            // 5b. Clear the bitmap around the swapped sites.
-            const int na = sh.n_acc;
-            const int per = 2 * (ztot + 1);
-            for (int x = tid; x < na * per; x += T) {
-                const uint32_t q = s_acc[x / per];
-                const int v = x % per;
-                const uint32_t c = (v <= ztot) ? s_qa[q] : s_qb[q];
-                const int vv = (v <= ztot) ? v : v - (ztot + 1);
-                const uint32_t site = (vv == 0) ? c : neighbour_of<KIND>(g, c, vv - 1);
-                atomicAnd(&s_bitmap[site >> 5], ~(1u << (site & 31)));
+            if (!take) continue;
+            __syncwarp();
+            for (int e = lane; e < E; e += 32) {
+                const int k = e / (S * S), i = (e / S) % S, j = e % S;
+                const int dl = entry_delta(gq[k], A, B, i, j);
+                if (dl == 0) continue;
+                const int n = m.cnt[e] + dl;
+                m.cnt[e] = n;
+                float_coefficient(e, n, (float)d.w[k], m.fQ, m.ft, m.fb, m.beta);
             }
+            mark_neighbourhood<KIND, true>(c.g, a, c.ztot, lane, 32, m.vec, m.bitmap);
+            mark_neighbourhood<KIND, true>(c.g, b, c.ztot, lane, 32, m.vec, m.bitmap);
+            if (lane == 0) {
+                store_species<BITS>(m.types, a, B);
+                store_species<BITS>(m.types, b, A);
+                m.acc[n_acc] = q;
+            }
+            ++n_acc;
+            __syncwarp();
         }
-        __syncthreads();
-        // Bookkeeping: depth counter, step budget, depth limit, time budget (Sec. 4.6.4).
-        if (tid == 0) {
-            const int na = sh.n_acc;
-            sh.accepted += na;
-            sh.depth = (na > 0) ? 0 : sh.depth + 1;
-            sh.steps += 1;
-            bool stop = sh.steps >= d.max_steps;
-            if (d.depth_limit > 0 && sh.depth >= d.depth_limit) stop = true;
-            if (d.timeout_ns > 0 && (int64_t)(globaltimer_ns() - sh.t0) >= d.timeout_ns) {
-                if (!stop) sh.status = HEA_ETIMEOUT;
-                stop = true;
-            }
-            sh.stop = stop ? 1 : 0;
-        }
-        __syncthreads();
+        if (lane == 0) sh.n_acc = n_acc;
     }
+    __syncthreads();
+}
 
-    // ---- write back ----
-    if (BITS == 8) {
-        for (uint32_t i = tid; i < N; i += T) d.types[i] = s_types[i];
-    } else {
-        for (uint32_t i = tid; i < N; i += T) d.types[i] = (uint8_t)load_species<4>(s_types, i);
+// After a walk: clear the bitmap around the swapped sites and refresh the binary64 coefficients
+// (and their FP32 roundings used by the next step's estimates) from the updated counts.
+template <int KIND>
+__device__ void after_walk(const ChainDesc& d, ChainSmem& m, ChainShared& sh, const ChainCtx& c) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int na = sh.n_acc;
+    for (int x = warp; x < 2 * na; x += nw) {
+        const uint32_t q = m.acc[x >> 1];
+        mark_neighbourhood<KIND, false>(c.g, (x & 1) ? m.qb[q] : m.qa[q], c.ztot, lane, 32, m.vec, m.bitmap);
     }
-    for (int e = tid; e < E; e += T) d.counts[e] = s_cnt[e];
-    if (tid == 0) {
-        double f2 = 0.0;
-        for (int e = 0; e < E; ++e) {
+    if (na > 0) {
+        const int S = c.S;
+        for (int e = threadIdx.x; e < c.E; e += blockDim.x) {
             const int k = e / (S * S);
-            const double err = __dsub_rn(__dsub_rn(1.0, __dmul_rn((double)s_cnt[e], s_Q[e])), s_t[e]);
+            const double err = __dsub_rn(__dsub_rn(1.0, __dmul_rn((double)m.cnt[e], m.Q[e])), m.tgt[e]);
+            const double b = __dmul_rn(-2.0, __dmul_rn(d.w[k], __dmul_rn(m.Q[e], err)));
+            m.cb[e] = b;
+            m.fb[e] = (float)b;
+        }
+    }
+    __syncthreads();
+}
+
+// Depth counter, step budget, depth limit, time budget (Sec. 4.6.4).
+__device__ __forceinline__ void bookkeeping(const ChainDesc& d, ChainShared& sh, bool timed_out) {
+    if (threadIdx.x == 0) {
+        const int na = sh.n_acc;
+        sh.accepted += na;
+        sh.depth = (na > 0) ? 0 : sh.depth + 1;
+        sh.steps += 1;
+        bool stop = sh.steps >= d.max_steps;
+        if (d.depth_limit > 0 && sh.depth >= d.depth_limit) stop = true;
+        if (timed_out) {
+            if (!stop) sh.status = HEA_ETIMEOUT;
+            stop = true;
+        }
+        sh.stop = stop ? 1 : 0;
+    }
+    __syncthreads();
+}
+
+template <int BITS>
+__device__ void write_back(const ChainDesc& d, ChainSmem& m, ChainShared& sh, const ChainCtx& c) {
+    const uint32_t N = c.N;
+    if (BITS == 8) {
+        for (uint32_t i = threadIdx.x; i < N; i += blockDim.x) d.types[i] = m.types[i];
+    } else {
+        for (uint32_t i = threadIdx.x; i < N; i += blockDim.x) d.types[i] = (uint8_t)load_species<4>(m.types, i);
+    }
+    for (int e = threadIdx.x; e < c.E; e += blockDim.x) d.counts[e] = m.cnt[e];
+    if (threadIdx.x == 0) {
+        const int S = c.S;
+        double f2 = 0.0;
+        for (int e = 0; e < c.E; ++e) {
+            const int k = e / (S * S);
+            const double err = __dsub_rn(__dsub_rn(1.0, __dmul_rn((double)m.cnt[e], m.Q[e])), m.tgt[e]);
             f2 = __dadd_rn(f2, __dmul_rn(d.w[k], __dmul_rn(err, err)));
         }
         d.result->steps = sh.steps;
-        d.result->trials = sh.steps * (int64_t)K;
+        d.result->trials = sh.steps * (int64_t)c.K;
         d.result->accepted = sh.accepted;
         d.result->depth = sh.depth;
         d.result->status = sh.status;
@@ -542,5 +736,206 @@ __device__ void run_chain(const ChainDesc& d, uint8_t* smem, ChainShared& sh) {
     }
 }
 
+__device__ __forceinline__ void report_invalid(const ChainDesc& d) {
+    if (threadIdx.x == 0) {
+        d.result->steps = 0;
+        d.result->trials = 0;
+        d.result->accepted = 0;
+        d.result->depth = d.depth0;
+        d.result->status = HEA_EINVAL;
+        d.result->f2 = CUDART_NAN;
+        d.result->f = CUDART_NAN;
+    }
+}
+
+// ------------------------------------------------------------------------------------------------
+// One chain, run to completion by the calling CTA.
+// ------------------------------------------------------------------------------------------------
+template <int KIND, int BITS>
+__device__ void run_chain(const ChainDesc& d, uint8_t* smem, ChainShared& sh) {
+    const ChainLayout L = chain_layout(d.N, d.M, d.S, d.qcap, BITS, d.accept_mode);
+    ChainSmem m(smem, L);
+    ChainCtx c;
+    chain_setup<KIND, BITS>(d, m, sh, c);
+    if (sh.bad) {
+        report_invalid(d);
+        return;
+    }
+    while (!sh.stop) {
+        const uint32_t step = d.step0 + (uint32_t)sh.steps;
+        if (threadIdx.x == 0) {
+            sh.qn = 0;
+            sh.n_acc = 0;
+            sh.win_q = -1;
+        }
+        __syncthreads();
+        const float my_umin = score_range<KIND, BITS>(d, m, sh, c, step, 0u, (uint32_t)c.K);
+        if (d.accept_mode == 0) {
+            const float umin = block_min(my_umin, sh);
+            best_of_queue<BITS>(m, sh, c, umin);
+            const int q = sh.win_q;
+            if (q >= 0) {
+                const uint32_t a = m.qa[q], b = m.qb[q];
+                const bool null_move = (a == b) || load_species<BITS>(m.types, a) == load_species<BITS>(m.types, b);
+                if (eligible(m.qD[q], null_move, c.thr)) apply_slot<BITS>(d, m, sh, c, q);
+            }
+        } else {
+            __syncthreads();
+            rank_eligible<BITS>(m, sh, c, sh.qn, d.group_size, d.group_top);
+            walk<KIND, BITS>(d, m, sh, c, sh.n_elig);
+            after_walk<KIND>(d, m, sh, c);
+        }
+        __syncthreads();
+        const bool timed_out = d.timeout_ns > 0 && (int64_t)(globaltimer_ns() - sh.t0) >= d.timeout_ns;
+        bookkeeping(d, sh, timed_out);
+    }
+    write_back<BITS>(d, m, sh, c);
+}
+
+// ------------------------------------------------------------------------------------------------
+// Cooperative chain: gridDim.x CTAs (all co-resident) share one chain.  CTA r scores candidates
+// [r Kc, (r+1) Kc) with Kc = K / gridDim.x and publishes its best (best-of-K: its argmin;
+// multi-accept: its group_top best eligible, the group being its slice); every CTA merges all
+// published candidates and applies the same accepted swaps to its own copy of the cell.
+// ------------------------------------------------------------------------------------------------
+__device__ __forceinline__ unsigned long long load_acquire(const unsigned long long* p) {
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Grid barrier on a monotonically increasing arrival counter.  The wait is bounded (2 s of
+// device time); a CTA whose wait runs out records the failure and reports it instead of spinning.
+static __device__ bool grid_barrier(CoopHeader* h, unsigned long long target, ChainShared& sh) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        atomicAdd(&h->arrive, 1ull);
+        const uint64_t t0 = globaltimer_ns();
+        bool ok = true;
+        while (load_acquire(&h->arrive) < target) {
+            if (globaltimer_ns() - t0 > 2000000000ull) {
+                ok = false;
+                atomicExch(&h->error, 1);
+                break;
+            }
+            __nanosleep(32);
+        }
+        __threadfence();
+        sh.sync_ok = ok ? 1 : 0;
+    }
+    __syncthreads();
+    return sh.sync_ok != 0;
+}
+
+template <int KIND, int BITS>
+__device__ void run_coop_chain(const ChainDesc& d, uint8_t* smem, ChainShared& sh) {
+    const ChainLayout L = chain_layout(d.N, d.M, d.S, d.qcap, BITS, d.accept_mode);
+    ChainSmem m(smem, L);
+    ChainCtx c;
+    chain_setup<KIND, BITS>(d, m, sh, c);
+    const int G = gridDim.x, rank = blockIdx.x, tid = threadIdx.x;
+    const int top = (d.accept_mode == 0) ? 1 : d.group_top;
+    const uint32_t Kc = (uint32_t)(c.K / G);
+    uint8_t* ws = static_cast<uint8_t*>(d.workspace);
+    CoopHeader* hdr = reinterpret_cast<CoopHeader*>(ws);
+    int32_t* counts_ws = reinterpret_cast<int32_t*>(ws + coop_counts_offset());
+    CoopRecord* recs = reinterpret_cast<CoopRecord*>(ws + coop_records_offset(G));
+    if (sh.bad) {   // identical in every CTA: the cell is the same
+        if (rank == 0) report_invalid(d);
+        return;
+    }
+    unsigned long long phase = 0;
+    while (!sh.stop) {
+        const uint32_t step = d.step0 + (uint32_t)sh.steps;
+        const int par = (int)(sh.steps & 1);
+        if (tid == 0) {
+            sh.qn = 0;
+            sh.n_acc = 0;
+            sh.win_q = -1;
+        }
+        __syncthreads();
+        const float my_umin = score_range<KIND, BITS>(d, m, sh, c, step, rank * Kc, (rank + 1) * Kc);
+        int n_pub = 0;
+        if (d.accept_mode == 0) {
+            const float umin = block_min(my_umin, sh);
+            best_of_queue<BITS>(m, sh, c, umin);
+            if (sh.win_q >= 0) {
+                m.order[0] = (uint32_t)sh.win_q;
+                n_pub = 1;
+            }
+        } else {
+            __syncthreads();
+            rank_eligible<BITS>(m, sh, c, sh.qn, (int)Kc, top);
+            n_pub = min(sh.n_elig, top);
+        }
+        // Publish this CTA's candidates for the step (double-buffered by step parity).
+        for (int x = tid; x < n_pub; x += blockDim.x) {
+            const uint32_t q = m.order[x];
+            CoopRecord* R = &recs[((size_t)par * G + rank) * kCoopMaxTop + x];
+            R->D = m.qD[q];
+            R->lo = m.qlo[q];
+            R->hi = m.qhi[q];
+            R->k = m.qk[q];
+            R->a = m.qa[q];
+            R->b = m.qb[q];
+            for (int k = 0; k < c.M; ++k) R->g[k] = m.qg[q * c.M + k];
+        }
+        if (tid == 0) {
+            counts_ws[par * G + rank] = n_pub;
+            if (rank == 0 && d.timeout_ns > 0 && (int64_t)(globaltimer_ns() - sh.t0) >= d.timeout_ns)
+                atomicExch(&hdr->stop, 1);
+        }
+        phase += 1;
+        if (!grid_barrier(hdr, phase * (unsigned long long)G, sh)) {
+            if (tid == 0) sh.status = HEA_ETIMEOUT;
+            __syncthreads();
+            break;
+        }
+        // Merge every CTA's published candidates into the local slots.
+        if (tid == 0) sh.qn = 0;
+        __syncthreads();
+        for (int x = tid; x < G * top; x += blockDim.x) {
+            const int r = x / top, i = x % top;
+            if (i >= __ldcg(&counts_ws[par * G + r])) continue;
+            const CoopRecord* R = &recs[((size_t)par * G + r) * kCoopMaxTop + i];
+            const int slot = atomicAdd(&sh.qn, 1);
+            m.qD[slot] = __ldcg(&R->D);
+            m.qlo[slot] = __ldcg(&R->lo);
+            m.qhi[slot] = __ldcg(&R->hi);
+            m.qk[slot] = __ldcg(&R->k);
+            m.qa[slot] = __ldcg(&R->a);
+            m.qb[slot] = __ldcg(&R->b);
+            for (int k = 0; k < c.M; ++k) m.qg[slot * c.M + k] = __ldcg(&R->g[k]);
+        }
+        __syncthreads();
+        if (d.accept_mode == 0) {
+            // Every CTA published its exact argmin: the global argmin over (D, k).
+            if (tid == 0) {
+                int best = -1;
+                for (int q = 0; q < sh.qn; ++q)
+                    if (best < 0 || better(m.qD[q], m.qk[q], m.qD[best], m.qk[best])) best = q;
+                sh.win_q = best;
+            }
+            __syncthreads();
+            const int q = sh.win_q;
+            if (q >= 0) {
+                const uint32_t a = m.qa[q], b = m.qb[q];
+                const bool null_move = (a == b) || load_species<BITS>(m.types, a) == load_species<BITS>(m.types, b);
+                if (eligible(m.qD[q], null_move, c.thr)) apply_slot<BITS>(d, m, sh, c, q);
+            }
+        } else {
+            // The published candidates are eligible; ranking them across CTAs computes exact keys
+            // where intervals from different CTAs overlap.
+            rank_eligible<BITS>(m, sh, c, sh.qn, 0, 0);
+            walk<KIND, BITS>(d, m, sh, c, sh.n_elig);
+            after_walk<KIND>(d, m, sh, c);
+        }
+        __syncthreads();
+        const bool timed_out = __ldcg(&hdr->stop) != 0;
+        bookkeeping(d, sh, timed_out);
+    }
+    if (rank == 0) write_back<BITS>(d, m, sh, c);
+}
 
 }  // namespace hea

@@ -36,7 +36,8 @@ class hea_search_params(ctypes.Structure):
     _fields_ = [("K", ctypes.c_int32), ("accept_mode", ctypes.c_int32), ("max_steps", ctypes.c_int64),
                 ("depth_limit", ctypes.c_int32), ("max_accept", ctypes.c_int32), ("threshold", ctypes.c_double),
                 ("seed", ctypes.c_uint64), ("chain", ctypes.c_uint32), ("step0", ctypes.c_uint32),
-                ("depth0", ctypes.c_int32), ("reserved", ctypes.c_int32), ("timeout_us", ctypes.c_int64)]
+                ("depth0", ctypes.c_int32), ("group_size", ctypes.c_int32), ("group_top", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("timeout_us", ctypes.c_int64)]
 
 
 class hea_search_result(ctypes.Structure):
@@ -77,6 +78,11 @@ def lib():
             "hea_search_batch_plan_bytes": (sz, [i32]),
             "hea_search_batch_plan": (i32, [i32, P, P, P, P, P, P, P]),
             "hea_search_batch": (i32, [P, P, P]),
+            "hea_search_coop_workspace_bytes": (sz, [i32]),
+            "hea_search_coop_max_ctas": (i32, [P, ctypes.POINTER(hea_objective), ctypes.POINTER(hea_search_params),
+                                               i32]),
+            "hea_search_coop": (i32, [P, ctypes.POINTER(hea_objective), ctypes.POINTER(hea_search_params), i32, P, P,
+                                      P, P, sz, P]),
             "hea_last_error": (ctypes.c_char_p, []),
             "hea_status_string": (ctypes.c_char_p, [i32]),
         }
@@ -176,15 +182,30 @@ def hea_delta_swap(lat, obj, types, counts, pairs, K, key, dcounts=None, stream=
 
 
 def search_params(K, max_steps, accept_mode=0, depth_limit=0, max_accept=0, threshold=0.0, seed=1, chain=0,
-                  step0=0, depth0=0, timeout_us=0):
+                  step0=0, depth0=0, group_size=0, group_top=0, timeout_us=0):
     return hea_search_params(K, accept_mode, max_steps, depth_limit, max_accept, threshold, seed, chain, step0,
-                             depth0, 0, timeout_us)
+                             depth0, group_size, group_top, 0, timeout_us)
 
 
 def hea_search(lat, obj, params, types, counts, result, stream=None):
     """`result` is a device buffer of RESULT_BYTES bytes (e.g. a uint8 tensor)."""
     _check(lib().hea_search(lat.handle, ctypes.byref(obj.c), ctypes.byref(params), _ptr(types), _ptr(counts),
                             _ptr(result), _stream(stream)))
+
+
+def hea_search_coop_workspace_bytes(ctas):
+    return int(lib().hea_search_coop_workspace_bytes(int(ctas)))
+
+
+def hea_search_coop_max_ctas(lat, obj, params, ctas):
+    return int(lib().hea_search_coop_max_ctas(lat.handle, ctypes.byref(obj.c), ctypes.byref(params), int(ctas)))
+
+
+def hea_search_coop(lat, obj, params, ctas, types, counts, result, workspace, stream=None):
+    """`workspace` is a device buffer of at least hea_search_coop_workspace_bytes(ctas) bytes."""
+    nbytes = workspace.numel() * workspace.element_size()
+    _check(lib().hea_search_coop(lat.handle, ctypes.byref(obj.c), ctypes.byref(params), int(ctas), _ptr(types),
+                                 _ptr(counts), _ptr(result), _ptr(workspace), nbytes, _stream(stream)))
 
 
 def decode_results(raw):

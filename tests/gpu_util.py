@@ -98,3 +98,20 @@ def gpu_search_batch(cells, params):
     hea.hea_search_batch(plan.host, plan_dev)
     torch.cuda.synchronize()
     return [t.cpu().numpy() for t in ts], [c.cpu().numpy() for c in cs], hea.decode_results(res.cpu().numpy())
+
+
+def sm_count():
+    return torch.cuda.get_device_properties(0).multi_processor_count
+
+
+def gpu_search_coop(kind, L, M, n_per, w, target, types, cnt, ctas, **kw):
+    ensure_built()
+    lat = hea.Lattice(kind, L, M)
+    obj = hea.Objective(n_per, w, target)
+    t = dev(np.asarray(types, np.uint8))
+    c = dev(np.asarray(cnt, np.int32))
+    res = torch.zeros(hea.RESULT_BYTES, dtype=torch.uint8, device="cuda")
+    ws = torch.zeros(hea.hea_search_coop_workspace_bytes(ctas), dtype=torch.uint8, device="cuda")
+    hea.hea_search_coop(lat, obj, hea.search_params(**kw), ctas, t, c, res, ws)
+    torch.cuda.synchronize()
+    return t.cpu().numpy(), c.cpu().numpy(), hea.decode_results(res.cpu().numpy())[0]

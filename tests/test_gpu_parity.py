@@ -328,3 +328,17 @@ def test_fcc_256k_multi_accept_matches_oracle_prefix():
     g, o = run_both(spec.kind, spec.L, spec.M, spec.S, spec.n_per, spec.weights(), spec.targets(), spec.seed,
                     K=SEARCH_K, max_steps=12, accept_mode=1, seed=1)
     assert_same(g, o)
+
+
+@pytest.mark.parametrize("kind,L,M,S,K,G,top,steps", [
+    (FCC, (8, 8, 8), 3, 4, 256, 32, 1, 40), (BCC, (10, 10, 10), 2, 5, 512, 64, 2, 30),
+    (FCC, (5, 6, 7), 3, 6, 1024, 256, 4, 15), (BCC, (4, 4, 4), 5, 3, 96, 17, 1, 50),
+])
+def test_search_multi_accept_group_rule_bit_exact(kind, L, M, S, K, G, top, steps):
+    N = oracle.num_sites(kind, L)
+    rng = np.random.default_rng(K + G)
+    n_per = composition(N, S, rng)
+    w, target = random_objective(M, S, rng, scale=0.8, symmetric=True)
+    g, o = run_both(kind, L, M, S, n_per, w, target, 3, K=K, max_steps=steps, accept_mode=1, group_size=G,
+                    group_top=top, seed=11)
+    assert_same(g, o)

@@ -186,3 +186,27 @@ def test_search_never_beats_exhaustive_minimum_and_finds_b2():
         _, _, res, _ = oracle.search(kind, L, M, n_per, w, b2, types, cnt, K=16, max_steps=200, seed=seed,
                                      depth_limit=20)
         assert res["f2"] >= f2_min
+
+
+def test_multi_accept_group_top_keeps_group_winners():
+    """With group_top = 1 the walk only sees the best eligible candidate of each group of
+    group_size consecutive candidates (checked against keys from the oracle's delta)."""
+    kind, L, M, S = ind.FCC, (6, 6, 6), 3, 4
+    N, n_per, types, cnt, w, target = setup(kind, L, M, S, 6, target_scale=0.8)
+    K, G = 256, 32
+    pairs = oracle.draw_pairs(N, 3, 0, 0, 1, K)
+    key, _, null = oracle.delta_swap(kind, L, M, n_per, w, target, types, cnt, pairs)
+    winners = set()
+    for g in range(K // G):
+        cand = [c for c in range(g * G, (g + 1) * G) if not null[c] and key[c] < 0]
+        if cand:
+            winners.add(min(cand, key=lambda c: (key[c], c)))
+    _, _, res, acc = oracle.search(kind, L, M, n_per, w, target, types, cnt, K=K, max_steps=1, accept_mode=1,
+                                   seed=3, group_size=G, group_top=1, log=True)
+    assert 0 < res["accepted"] <= len(winners)
+    assert {tuple(x) for x in acc} <= {tuple(pairs[c]) for c in winners}
+    # group_top >= group_size keeps everything: same as the plain rule.
+    a = oracle.search(kind, L, M, n_per, w, target, types, cnt, K=K, max_steps=3, accept_mode=1, seed=3)
+    b = oracle.search(kind, L, M, n_per, w, target, types, cnt, K=K, max_steps=3, accept_mode=1, seed=3,
+                      group_size=G, group_top=G)
+    assert np.array_equal(a[0], b[0]) and a[2]["f2"] == b[2]["f2"]
