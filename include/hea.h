@@ -222,6 +222,26 @@ hea_status hea_search_coop(const hea_lattice* lat, const hea_objective* obj, con
                            int ctas, uint8_t* types, int32_t* counts, hea_search_result* result, void* workspace,
                            size_t workspace_bytes, void* stream);
 
+/*
+ * hea_search_coop without caller memory, for callers that cannot allocate device memory (a
+ * process whose device memory belongs to another runtime's allocator, a plugin host that forbids
+ * cudaMalloc, a deployment with a fixed device-memory budget).  The paper has no counterpart: the
+ * exchange area of the cooperative search lives in a fixed array of HEA_NOALLOC_SCRATCH_BYTES
+ * bytes inside the library's device image, held by every GPU that loads the library until the
+ * process exits.  Nothing is allocated.
+ *   - ctas must need at most HEA_NOALLOC_SCRATCH_BYTES of exchange area (up to 512 CTAs);
+ *     larger requests return HEA_EINVAL before any launch.
+ *   - The array is shared by every call on a device and keeps the last call's contents; each call
+ *     clears the barrier header on `stream` before launching.  Calls that overlap on the GPU race
+ *     on the array: serialise them.
+ *   - The first call on a device (with that device current) looks up the array's address once;
+ *     make that first call before any stream capture.
+ * Other arguments, results and errors: as hea_search_coop.
+ */
+#define HEA_NOALLOC_SCRATCH_BYTES 307200
+hea_status hea_search_coop_noalloc(const hea_lattice* lat, const hea_objective* obj, const hea_search_params* params,
+                                   int ctas, uint8_t* types, int32_t* counts, hea_search_result* result, void* stream);
+
 /* Message for the last error returned on the calling thread ("" if none). */
 const char* hea_last_error(void);
 const char* hea_status_string(int status);

@@ -154,6 +154,10 @@ size_t plan_offset() { return hea::align_up(sizeof(PlanHeader), 256); }
 
 }  // namespace
 
+namespace hea {
+hea_status set_last_error(hea_status status, const char* message) { return fail(status, "%s", message); }
+}  // namespace hea
+
 extern "C" {
 
 const char* hea_last_error(void) { return g_err; }

@@ -110,6 +110,9 @@ __host__ __device__ inline size_t coop_workspace_bytes(int ctas) {
     return coop_records_offset(ctas) + 2 * (size_t)ctas * kCoopMaxTop * sizeof(CoopRecord);
 }
 
+// Records `message` as the calling thread's hea_last_error() text and returns `status`.
+hea_status set_last_error(hea_status status, const char* message);
+
 // Launchers implemented in the .cu files.
 cudaError_t launch_init_config(int kind, int Lx, int Ly, int Lz, int S, const int64_t* cum, uint64_t seed,
                                uint8_t* types, cudaStream_t stream);

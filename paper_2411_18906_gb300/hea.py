@@ -83,6 +83,8 @@ def lib():
                                                i32]),
             "hea_search_coop": (i32, [P, ctypes.POINTER(hea_objective), ctypes.POINTER(hea_search_params), i32, P, P,
                                       P, P, sz, P]),
+            "hea_search_coop_noalloc": (i32, [P, ctypes.POINTER(hea_objective), ctypes.POINTER(hea_search_params),
+                                              i32, P, P, P, P]),
             "hea_last_error": (ctypes.c_char_p, []),
             "hea_status_string": (ctypes.c_char_p, [i32]),
         }
@@ -206,6 +208,12 @@ def hea_search_coop(lat, obj, params, ctas, types, counts, result, workspace, st
     nbytes = workspace.numel() * workspace.element_size()
     _check(lib().hea_search_coop(lat.handle, ctypes.byref(obj.c), ctypes.byref(params), int(ctas), _ptr(types),
                                  _ptr(counts), _ptr(result), _ptr(workspace), nbytes, _stream(stream)))
+
+
+def hea_search_coop_noalloc(lat, obj, params, ctas, types, counts, result, stream=None):
+    """hea_search_coop with the library's fixed exchange area (no device memory from the caller)."""
+    _check(lib().hea_search_coop_noalloc(lat.handle, ctypes.byref(obj.c), ctypes.byref(params), int(ctas),
+                                         _ptr(types), _ptr(counts), _ptr(result), _stream(stream)))
 
 
 def decode_results(raw):
