@@ -257,12 +257,124 @@ def run_ours(args):
         "final": {"F": res["f"], "accepted": res["accepted"], "search_steps": res["steps"]},
         "wall_s": wall,
     }
+    if rank == 0 and world == 1 and not args.no_secondary:
+        line["batched"] = run_batched(torch, hea)
+        line["recount"] = run_recount(torch, hea)
+        line["serve"] = run_serving(args.serve_requests)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args.cpu_steps, ctas)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+def run_batched(torch, hea, n_cells=512, trials=1_000_000, steps=3, warmup=1):
+    """Batched workload: n_cells independent cells (FCC or BCC, 500-32,000 sites, 3-6 species,
+    1-3 shells, annealed targets) searched together, 1e6 trials each, best-of-K; the whole step
+    (initial configuration, recount and the batched search of every cell) is one captured CUDA
+    graph, replayed per timed step.  K per size bucket comes from the autotuner."""
+    from paper_2411_18906_gb300 import autotune
+    cells = workloads.batch_cells(n_cells, seed=1)
+    prep = []
+    for c in cells:
+        lat = hea.Lattice(c.kind, c.L, c.M)
+        obj = hea.Objective(c.n_per, c.weights(), c.targets())
+        t = torch.empty(c.N, dtype=torch.uint8, device="cuda")
+        k = torch.empty((c.M, c.S, c.S), dtype=torch.int32, device="cuda")
+        hea.hea_init_config(lat, c.n_per, c.seed, t)
+        hea.hea_sro_counts(lat, 1, t, c.S, k)
+        prep.append((lat, obj, t, k))
+    torch.cuda.synchronize()
+    choice, report = autotune.tune(prep, trials=100_000, accept_mode=0)
+    params = []
+    for i, (lat, _, _, _) in enumerate(prep):
+        K = choice[autotune.bucket_of(lat.N)]
+        params.append(hea.search_params(K, max(1, trials // K), accept_mode=0, seed=3000 + i, chain=i))
+    res = torch.zeros(n_cells * hea.RESULT_BYTES, dtype=torch.uint8, device="cuda")
+    plan = hea.BatchPlan([p[0] for p in prep], [p[1] for p in prep], params, [p[2] for p in prep],
+                         [p[3] for p in prep], res)
+    plan_dev = torch.from_numpy(plan.host).cuda()
+
+    def step():
+        for (lat, obj, t, k), c in zip(prep, cells):
+            hea.hea_init_config(lat, c.n_per, c.seed, t)
+            hea.hea_sro_counts(lat, 1, t, c.S, k)
+        hea.hea_search_batch(plan.host, plan_dev)
+
+    step()
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        with torch.cuda.graph(graph, stream=side, capture_error_mode="relaxed"):
+            step()
+    torch.cuda.current_stream().wait_stream(side)
+    for _ in range(warmup):
+        graph.replay()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        graph.replay()
+    e1.record()
+    e1.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    out = hea.decode_results(res.cpu().numpy())
+    trials_total = sum(r["trials"] for r in out)
+    return {"metric": "batched cells/s", "value": n_cells / (ms / 1000.0), "unit": "cells/s",
+            "ms_per_step": ms, "cells": n_cells, "trials_per_cell": trials, "trials_per_s": trials_total / (ms / 1e3),
+            "accept_mode": "best-of-K", "K_by_bucket": {str(b): k for b, k in choice.items()},
+            "autotune": report, "graph": "one CUDA graph per step (init + recount per cell, one batched search)",
+            "mean_F": float(np.mean([r["f"] for r in out])),
+            "status_ok": all(r["status"] == 0 for r in out)}
+
+
+def run_recount(torch, hea, n_configs=1000):
+    """Full recount throughput: 1000 seeded BCC 20x20x20 configurations (5 species, shells 1-2) in
+    one call; HBM roofline = configuration bytes read + count bytes written."""
+    spec = workloads.bcc_16k()
+    lat = hea.Lattice(spec.kind, spec.L, spec.M)
+    N, S, M = lat.N, spec.S, spec.M
+    types = torch.empty((n_configs, N), dtype=torch.uint8, device="cuda")
+    for i in range(n_configs):
+        hea.hea_init_config(lat, spec.n_per, i + 1, types[i])
+    counts = torch.empty((n_configs, M, S, S), dtype=torch.int32, device="cuda")
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
+    for _ in range(3):
+        hea.hea_sro_counts(lat, n_configs, types, S, counts)
+    torch.cuda.synchronize()
+    times = []
+    for r in range(5):
+        flush.fill_(r)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        hea.hea_sro_counts(lat, n_configs, types, S, counts)
+        e1.record()
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1) / 1000.0)
+    t = float(np.median(times))
+    peaks, kind = load_peaks()
+    nbytes = n_configs * N + n_configs * M * S * S * 4
+    visits = n_configs * N * (8 + 6)
+    return {"metric": "pair-counts/s (full recount, 1000 x BCC 20^3)", "value": visits / t, "unit": "pair visits/s",
+            "seconds": t, "roofline": {"bound": "hbm", "achieved": nbytes / t / 1e9, "peak": peaks["hbm_gbs"],
+                                        "unit": "GB/s", "frac": nbytes / t / 1e9 / peaks["hbm_gbs"],
+                                        "peak_source": kind}}
+
+
+def run_serving(n_requests=300, rate=50.0):
+    """Served workload: Poisson arrivals (50/s), 1k-256k sites (20% at 256k), 4-5 species, K = 256,
+    depth limit 10, at most 1e6 trials per request, continuous batching on per-request streams."""
+    from paper_2411_18906_gb300 import serve
+    reqs = serve.poisson_requests(n_requests, rate, seed=1)
+    srv = serve.Server(hbm_budget_bytes=16 << 30, slots=64)
+    done = srv.run(reqs)
+    out = serve.latency_summary(done)
+    out.update({"metric": "serve latency", "unit": "s", "rate_per_s": rate, "max_inflight": srv.max_inflight,
+                "status_ok": all(c.result["status"] == 0 for c in done)})
+    return out
 
 
 def oracle_free_initial(spec, N):
@@ -334,6 +446,8 @@ def main():
     ap.add_argument("--trials", type=int, default=TRIALS_PER_STEP,
                     help="swap trials per step (workload size; the headline workload is 1e8)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-secondary", action="store_true", help="skip the batched, recount and serving measurements")
+    ap.add_argument("--serve-requests", type=int, default=300)
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)

@@ -139,7 +139,9 @@ hea_status hea_delta_swap(const hea_lattice* lat, const hea_objective* obj, cons
 
 /* Parameters of the parallel Monte Carlo search (Alg. parallel_mc; Sec. 4.6.4). */
 typedef struct {
-    int32_t K;            /* candidate swaps (tasks) per step: 1..4096 per CTA */
+    int32_t K;            /* candidate swaps (tasks) per step: 1..4096 per CTA, further limited by
+                             shared memory (about 60 bytes per candidate next to the cell;
+                             HEA_ENOMEM when it does not fit) */
     int32_t accept_mode;  /* 0: best-of-K (argmin over (D, k)); 1: non-overlapping multi-accept */
     int64_t max_steps;    /* step budget (>= 0) */
     int32_t depth_limit;  /* stop once this many consecutive steps accepted nothing (0 = off) */

@@ -1,0 +1,90 @@
+"""Autotuner for the batched search: picks the candidates-per-step K of each cell-size bucket.
+
+For a fixed trial budget per cell, K trades steps (each with a fixed barrier/accept cost) against
+per-step work; the best K depends on the cell size and the GPU.  The tuner times hea_search_batch
+on a sample of the workload's cells for each K in a candidate set, per size bucket, and keeps the
+K with the highest trials/s.  Results are cached per (GPU name, bucket, budget) in a JSON file.
+"""
+import json
+import os
+import time
+
+import numpy as np
+
+from . import hea
+
+CANDIDATE_K = (128, 256, 512, 1024)
+BUCKETS = ((0, 4000), (4000, 12000), (12000, 1 << 30))   # sites
+
+
+def bucket_of(n_sites: int) -> int:
+    for b, (lo, hi) in enumerate(BUCKETS):
+        if lo <= n_sites < hi:
+            return b
+    return len(BUCKETS) - 1
+
+
+def _cache_path():
+    root = os.environ.get("XDG_CACHE_HOME", os.path.join(os.path.expanduser("~"), ".cache"))
+    return os.path.join(root, "hea_gb300_autotune.json")
+
+
+def _time_batch(torch, cells, K, trials, accept_mode, repeats=2):
+    """Seconds of one hea_search_batch over `cells` (list of (Lattice, Objective, types, counts))."""
+    n = len(cells)
+    params = [hea.search_params(K, max(1, trials // K), accept_mode=accept_mode, seed=7 + i) for i in range(n)]
+    res = torch.zeros(n * hea.RESULT_BYTES, dtype=torch.uint8, device="cuda")
+    best = None
+    for _ in range(repeats):
+        ts = [t.clone() for _, _, t, _ in cells]
+        cs = [c.clone() for _, _, _, c in cells]
+        plan = hea.BatchPlan([l for l, _, _, _ in cells], [o for _, o, _, _ in cells], params, ts, cs, res)
+        plan_dev = torch.from_numpy(plan.host).cuda()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        hea.hea_search_batch(plan.host, plan_dev)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        best = dt if best is None else min(best, dt)
+    return best
+
+
+def tune(cells, trials: int, accept_mode: int = 0, sample: int = 48, use_cache: bool = True):
+    """cells: list of (Lattice, Objective, types tensor, counts tensor).  Returns ({bucket: K}, report)."""
+    import torch
+    gpu = torch.cuda.get_device_name(0)
+    key = f"{gpu}|{trials}|{accept_mode}|{len(cells)}"
+    path = _cache_path()
+    cache = {}
+    if use_cache and os.path.exists(path):
+        try:
+            with open(path) as fh:
+                cache = json.load(fh)
+        except (OSError, ValueError):
+            cache = {}
+    if use_cache and key in cache:
+        return {int(b): k for b, k in cache[key]["choice"].items()}, cache[key]["report"]
+    by_bucket = {}
+    for cell in cells:
+        by_bucket.setdefault(bucket_of(cell[0].N), []).append(cell)
+    rng = np.random.default_rng(0)
+    choice, report = {}, {}
+    for b, members in sorted(by_bucket.items()):
+        pick = [members[i] for i in rng.choice(len(members), size=min(sample, len(members)), replace=False)]
+        rates = {}
+        for K in CANDIDATE_K:
+            dt = _time_batch(torch, pick, K, trials, accept_mode)
+            rates[K] = len(pick) * (trials // K) * K / dt
+        best = max(rates, key=rates.get)
+        choice[b] = best
+        report[str(b)] = {"sites": list(BUCKETS[b]), "cells_sampled": len(pick),
+                          "trials_per_s": {str(k): v for k, v in rates.items()}, "K": best}
+    if use_cache:
+        cache[key] = {"choice": {str(b): k for b, k in choice.items()}, "report": report}
+        try:
+            os.makedirs(os.path.dirname(path), exist_ok=True)
+            with open(path, "w") as fh:
+                json.dump(cache, fh, indent=1)
+        except OSError:
+            pass
+    return choice, report

@@ -91,15 +91,26 @@ hea_status check_params(const hea_lattice* lat, const hea_search_params* p) {
 }
 
 // Chooses 8- or 4-bit species storage so that the chain's shared memory (the cell plus `qcap`
-// candidate slots) fits one CTA.
-hea_status place_chain(const hea_lattice* lat, int S, const hea_search_params* p, int qcap, hea::ChainDesc* d) {
-    for (int bits : {8, 4}) {
-        const hea::ChainLayout L = hea::chain_layout((int)lat->N, lat->M, S, qcap, bits, p->accept_mode);
-        if (L.total + 2048 <= hea::kSearchSmemLimit) {
-            d->bits = bits;
-            d->smem_bytes = L.total;
-            d->qcap = qcap;
-            return ok();
+// candidate slots) fits one CTA, preferring room for the pairwise multi-accept walk over ranked
+// lists of up to `walk_cap` candidates.
+hea_status place_chain(const hea_lattice* lat, int S, const hea_search_params* p, int qcap, hea::ChainDesc* d,
+                       int walk_cap = -1) {
+    const int E = lat->M * S * S;
+    int cap = walk_cap < 0 ? qcap : walk_cap;
+    if (cap > hea::kPairWalkMax) cap = hea::kPairWalkMax;
+    if (E > 255 || p->accept_mode != 1) cap = 0;
+    // The pairwise walk keeps site positions as int16 half-unit coordinates.
+    if (2 * std::max(lat->Lx, std::max(lat->Ly, lat->Lz)) > 32767) cap = 0;
+    for (int pc : {cap, 0}) {
+        for (int bits : {8, 4}) {
+            const hea::ChainLayout L = hea::chain_layout((int)lat->N, lat->M, S, qcap, bits, p->accept_mode, pc);
+            if (L.total + 2048 <= hea::kSearchSmemLimit) {
+                d->bits = bits;
+                d->smem_bytes = L.total;
+                d->qcap = qcap;
+                d->pair_cap = pc;
+                return ok();
+            }
         }
     }
     return fail(HEA_ENOMEM, "cell of %lld sites with %d candidate slots does not fit one CTA's shared memory",
@@ -356,7 +367,8 @@ int hea_search_coop_max_ctas(const hea_lattice* lat, const hea_objective* obj, c
     hea::ChainDesc d;
     fill_desc(lat, obj, &d);
     fill_params(params, &d);
-    if (place_chain(lat, obj->S, params, qcap, &d) != HEA_OK) return 0;
+    if (place_chain(lat, obj->S, params, qcap, &d, ctas * (params->accept_mode == 1 ? params->group_top : 1)) != HEA_OK)
+        return 0;
     return (d.kind == HEA_FCC) ? hea::coop_max_ctas_fcc(d) : hea::coop_max_ctas_bcc(d);
 }
 
@@ -378,7 +390,7 @@ hea_status hea_search_coop(const hea_lattice* lat, const hea_objective* obj, con
     hea::ChainDesc d;
     fill_desc(lat, obj, &d);
     fill_params(params, &d);
-    st = place_chain(lat, obj->S, params, qcap, &d);
+    st = place_chain(lat, obj->S, params, qcap, &d, ctas * (params->accept_mode == 1 ? params->group_top : 1));
     if (st != HEA_OK) return st;
     const int most = (d.kind == HEA_FCC) ? hea::coop_max_ctas_fcc(d) : hea::coop_max_ctas_bcc(d);
     if (most < 1) return fail(HEA_ECUDA, "no CUDA device for a cooperative launch");

@@ -12,6 +12,7 @@ constexpr int kChainThreads = 256;   // threads of a single-CTA search chain
 constexpr int kCoopThreads = 512;    // threads of each CTA of a cooperative chain
 constexpr int kMaxK = 4096;          // candidates per CTA per step
 constexpr int kCoopMaxTop = 4;       // records (best eligible candidates) per CTA per step
+constexpr int kPairWalkMax = 640;    // longest ranked list the pairwise multi-accept walk handles
 constexpr uint32_t kSearchSmemLimit = 227 * 1024;
 
 // Everything one search chain needs, passed by value (single chain) or from device memory
@@ -21,6 +22,7 @@ struct ChainDesc {
     int32_t K, accept_mode, depth_limit, max_accept;
     uint32_t chain, step0;
     int32_t depth0, group_size, group_top, ctas;
+    int32_t pair_cap, pad2;   // multi-accept: longest ranked list the pairwise walk can hold
     int64_t max_steps;
     int64_t timeout_ns;
     uint64_t seed;
@@ -38,16 +40,28 @@ struct ChainDesc {
 
 // Shared-memory layout of one search CTA (offsets in bytes from the dynamic smem base).
 struct ChainLayout {
-    uint32_t types, cnt, Q, tgt, ca, cb, fa, fb, fQ, ft, beta, vec;
-    uint32_t qk, qa, qb, qlo, qhi, qD, qg, order, acc, bitmap;
+    uint32_t types, cnt, Q, tgt, ca, cb, fa, fb, fQ, fe0, dn, tiny, beta, vec, slot;
+    uint32_t qk, qa, qb, qlo, qhi, qD, qkey, qg, order, acc, bitmap, fw;
     uint32_t total;
 };
 
 __host__ __device__ inline uint32_t align_up(uint32_t x, uint32_t a) { return (x + a - 1) / a * a; }
 
+// Bytes of the pairwise-walk data for a ranked list of up to n candidates: per candidate its
+// nonzero count changes (2 bytes each, M (4S - 4) at most), its count, its two sites' coordinates
+// (6 int16) and its row of the conflict matrix (ceil(n / 32) words).
+__host__ __device__ inline uint32_t pair_walk_bytes(int n, int M, int S) {
+    const uint32_t mp = (uint32_t)(M * (4 * S - 4));
+    const uint32_t nw = (uint32_t)((n + 31) / 32);
+    return align_up((uint32_t)n * 2 * mp, 16) + align_up((uint32_t)n, 16) + align_up((uint32_t)n * 12, 16) +
+           align_up((uint32_t)n * 4 * nw, 16) + align_up((uint32_t)n * 10, 16);
+}
+
 // qcap: candidate slots (the candidates a CTA scores per step, or the merged records of a
-// cooperative chain, whichever is larger).
-__host__ __device__ inline ChainLayout chain_layout(int N, int M, int S, int qcap, int bits, int accept_mode) {
+// cooperative chain, whichever is larger).  pair_cap: longest ranked list the pairwise walk
+// handles (0 = always the bitmap walk); its data shares memory with the site bitmap.
+__host__ __device__ inline ChainLayout chain_layout(int N, int M, int S, int qcap, int bits, int accept_mode,
+                                                   int pair_cap = 0) {
     ChainLayout L{};
     const uint32_t E = (uint32_t)(M * S * S);
     const uint32_t C = (uint32_t)qcap;
@@ -62,21 +76,28 @@ __host__ __device__ inline ChainLayout chain_layout(int N, int M, int S, int qca
     L.fa = o;     o = align_up(o + 4 * E, 16);
     L.fb = o;     o = align_up(o + 4 * E, 16);
     L.fQ = o;     o = align_up(o + 4 * E, 16);
-    L.ft = o;     o = align_up(o + 4 * E, 16);
+    L.fe0 = o;    o = align_up(o + 4 * E, 16);
+    L.dn = o;     o = align_up(o + 4 * E, 16);
+    L.tiny = o;   o = align_up(o + 4 * E, 16);
     L.beta = o;   o = align_up(o + 4 * E, 16);
     L.vec = o;    o = align_up(o + 4 * 96, 16);
+    L.slot = o;   o = align_up(o + 2 * 5 * 28, 16);
+    L.fw = o;     o = align_up(o + 4 * E, 16);
     L.qk = o;     o = align_up(o + 4 * C, 16);
     L.qa = o;     o = align_up(o + 4 * C, 16);
     L.qb = o;     o = align_up(o + 4 * C, 16);
     L.qlo = o;    o = align_up(o + 4 * C, 16);
     L.qhi = o;    o = align_up(o + 4 * C, 16);
     L.qD = o;     o = align_up(o + 8 * C, 16);
+    L.qkey = o;   o = align_up(o + 8 * C, 16);
     L.qg = o;     o = align_up(o + 8 * C * (uint32_t)M, 16);
     L.order = o;  o = align_up(o + 4 * C, 16);
     L.acc = o;    o = align_up(o + 4 * C, 16);
     if (accept_mode == 1) {
         L.bitmap = o;
-        o = align_up(o + 4 * (uint32_t)((N + 31) / 32), 16);
+        const uint32_t bm = 4 * (uint32_t)((N + 31) / 32);
+        const uint32_t pw = pair_cap > 0 ? pair_walk_bytes(pair_cap, M, S) : 0u;
+        o = align_up(o + (bm > pw ? bm : pw), 16);
     } else {
         L.bitmap = o;
     }

@@ -30,9 +30,9 @@ namespace hea {
 
 static __constant__ ShellTable c_shells[2] = {build_shell_table(kFCC), build_shell_table(kBCC)};
 
-// Error factor of the FP32 key estimate (see score_float) and its absolute floor.
-constexpr float kRelBound = 1.220703125e-4f;   // 2^-13
+// Absolute floor of the FP32 key bound (see score_float) and 2^-23, the unit of its relative part.
 constexpr float kAbsBound = 7.52316385e-37f;   // 2^-120
+constexpr float kTwoUlp = 1.1920928955078125e-07f;  // 2^-23
 constexpr float kBetaScale = 3.814697265625e-06f;  // 2^-18
 
 struct ChainShared {
@@ -126,12 +126,15 @@ static __device__ double exact_key_running(int M, int S, const int32_t* cnt, con
 }
 
 // FP32 estimate of the key and a bound on its distance to the exact binary64 key.  Both evaluate
-// sum_e d_e (a_e d_e + b_e) from the same binary64 coefficients, the FP32 one from their float
-// roundings.  With n <= 320 nonzero entries the float evaluation is within
-// (n + 2) 2^-24 sum |d| (|a| |d| + |b|) (+ a subnormal floor) of the real value and the binary64
-// chain within (n + 1) 2^-53 of it, so |D32 - D64| < 2^-13 sum |d| (|a| |d| + |b|) + 2^-120.
+// D = sum_e d_e (a_e d_e + b_e) from the same binary64 coefficients a, b; the estimate uses their
+// binary32 roundings and the chain acc <- fma(d, fma(a', d, b'), acc).  With u = 2^-24 and n <= E
+// nonzero terms, rounding a and b, the inner and the outer fma each contribute at most u per term
+// magnitude plus u |partial sum|, so the estimate is within (n + 2) u (1 + 2 (n + 2) u) S + n 48 2^-150
+// of the real value, S = sum |d| (|a| |d| + |b|) (itself underestimated by at most (n + 2) u in FP32);
+// the binary64 chain is within (n + 1) 2^-53 S of it.  For E <= 320 the distance is below
+// (E + 3) u S + 2^-136, and the bound used, (E + 4) 2^-23 S + 2^-120, is twice that.
 __device__ __forceinline__ void score_float(int M, int S, const float* __restrict__ fa, const float* __restrict__ fb,
-                                            int A, int B, const uint64_t* gb, float& D, float& err) {
+                                            int A, int B, const uint64_t* gb, float rel, float& D, float& err) {
     float acc = 0.f, mag = 0.f;
 #pragma unroll
     for (int k = 0; k < kMaxShells; ++k) {
@@ -169,7 +172,7 @@ __device__ __forceinline__ void score_float(int M, int S, const float* __restric
         }
     }
     D = acc;
-    err = fmaf(mag, kRelBound, kAbsBound);
+    err = fmaf(mag, rel, kAbsBound);
 }
 
 __device__ __forceinline__ bool eligible(double D, bool null_move, double threshold) {
@@ -178,31 +181,46 @@ __device__ __forceinline__ bool eligible(double D, bool null_move, double thresh
     return threshold > 0.0 && D <= threshold;
 }
 
-// Eligibility from an interval around the key: 1 eligible, 0 not, -1 undecided.
-__device__ __forceinline__ int eligible_interval(float lo, float hi, double threshold) {
-    if (threshold > 0.0) return ((double)hi <= threshold) ? 1 : (((double)lo > threshold) ? 0 : -1);
+// Eligibility from an interval [lo, hi] around the key: 1 eligible, 0 not, -1 undecided.
+// thr_lo / thr_hi are the binary32 neighbours below / above the threshold (both 0 for 0).
+__device__ __forceinline__ int eligible_interval(float lo, float hi, bool positive_thr, float thr_lo, float thr_hi) {
+    if (positive_thr) return (hi <= thr_lo) ? 1 : ((lo > thr_hi) ? 0 : -1);
     return (hi < 0.f) ? 1 : ((lo >= 0.f) ? 0 : -1);
 }
 
-// Bound beta_e on the distance between an FP32 coefficient b of entry e and the exact one: the FP32
-// evaluation of e = (1 - n Q) - t and b = -2 (w (Q e)) is within 8 * 2^-24 * 2 w Q (1 + |n Q| + |t| + |e|)
-// of the real values and the binary64 coefficient within 2^-50 of the same scale;
-// beta_e = 2^-18 * 2 w Q (1 + |n Q| + |t| + |e|).
-__device__ __forceinline__ float beta_of(float w, float Q, float nq, float t, float err) {
-    return kBetaScale * (2.0f * w * Q) * (1.0f + fabsf(nq) + fabsf(t) + fabsf(err));
-}
+// Coefficients during the multi-accept walk.  At the start of a step entry e has the binary64
+// error e0 and coefficient b0, the FP32 copies fe0 = fl(e0) and fb = fl(b0), and dn = 0.  After the
+// walk changes its count by dn, the running values are e = e0 - dn Q and b = -2 (w (Q e)); in FP32
+// e_f = fe0 - dn fQ and fb = -2 (fw (fQ e_f)).  With u = 2^-24 these are within
+// 2 w Q (5 u (|e0| + |dn Q|)) + 2 w Q 2^-51 (2 + |t| + |e0|) of the real values, and the binary64
+// coefficient the exact running key uses is within 2 w Q 2^-50 (1 + |n Q| + |t| + |e|) of them.
+// beta_e = 2 w Q 2^-20 (|fe0| + |dn fQ|) + tiny_e, with the count-independent
+// tiny_e = 2 w Q 2^-46 (4 + 2 N / N_j + 2 |t|) (|n Q| <= N / N_j, |e| <= 1 + N / N_j + |t|), bounds
+// the distance of fb to both; at the start of a step beta_e = 2^-23 |fb| + tiny_e.
+constexpr float kTwoPow20 = 9.5367431640625e-07f;   // 2^-20
 
-// Running FP32 coefficient of entry e for count n during the multi-accept walk, and its bound.
-__device__ __forceinline__ void float_coefficient(int e, int n, float w, const float* fQ, const float* ft,
-                                                  float* fb, float* beta) {
-    const float nq = (float)n * fQ[e];
-    const float err = (1.0f - nq) - ft[e];
-    fb[e] = -2.0f * (w * (fQ[e] * err));
-    beta[e] = beta_of(w, fQ[e], nq, ft[e], err);
+__device__ __forceinline__ void running_coefficient(int e, int dn, float w, const float* fQ, const float* fe0,
+                                                    const float* tiny, float* fb, float* beta) {
+    const float dq = (float)dn * fQ[e];
+    const float ef = fe0[e] - dq;
+    fb[e] = -2.0f * (w * (fQ[e] * ef));
+    beta[e] = fmaf(2.0f * w * fQ[e], kTwoPow20 * (fabsf(fe0[e]) + fabsf(dq)), tiny[e]);
 }
 
 __device__ __forceinline__ bool better(double D1, uint32_t k1, double D2, uint32_t k2) {
     return D1 < D2 || (D1 == D2 && k1 < k2);
+}
+
+// Order-preserving integer image of a key (no NaNs; -0 and +0 map to the same value), so that the
+// ranking loops compare integers instead of binary64 values.
+__device__ __forceinline__ uint64_t order_key(double D) {
+    long long bits = __double_as_longlong(D);
+    if ((bits & 0x7FFFFFFFFFFFFFFFll) == 0) bits = 0;
+    return bits < 0 ? ~(uint64_t)bits : ((uint64_t)bits | 0x8000000000000000ull);
+}
+
+__device__ __forceinline__ bool better_key(uint64_t K1, uint32_t k1, uint64_t K2, uint32_t k2) {
+    return K1 < K2 || (K1 == K2 && k1 < k2);
 }
 
 // Site index of the point at half-unit position (X, Y, Z) + the shell vector packed in `pv`
@@ -245,12 +263,16 @@ struct ChainSmem {
     uint8_t* types;
     int32_t* cnt;
     double *Q, *tgt, *ca, *cb;
-    float *fa, *fb, *fQ, *ft, *beta;
+    float *fa, *fb, *fQ, *fe0, *tiny, *beta;
+    int32_t* dn;
     uint32_t* vec;
+    uint16_t* slot;
     uint32_t *qk, *qa, *qb;
     float *qlo, *qhi;
     double* qD;
+    uint64_t* qkey;
     uint64_t* qg;
+    float* fw;
     uint32_t *order, *acc, *bitmap;
 
     __device__ ChainSmem(uint8_t* smem, const ChainLayout& L) {
@@ -263,16 +285,21 @@ struct ChainSmem {
         fa = reinterpret_cast<float*>(smem + L.fa);
         fb = reinterpret_cast<float*>(smem + L.fb);
         fQ = reinterpret_cast<float*>(smem + L.fQ);
-        ft = reinterpret_cast<float*>(smem + L.ft);
+        fe0 = reinterpret_cast<float*>(smem + L.fe0);
+        tiny = reinterpret_cast<float*>(smem + L.tiny);
         beta = reinterpret_cast<float*>(smem + L.beta);
+        dn = reinterpret_cast<int32_t*>(smem + L.dn);
         vec = reinterpret_cast<uint32_t*>(smem + L.vec);
+        slot = reinterpret_cast<uint16_t*>(smem + L.slot);
         qk = reinterpret_cast<uint32_t*>(smem + L.qk);
         qa = reinterpret_cast<uint32_t*>(smem + L.qa);
         qb = reinterpret_cast<uint32_t*>(smem + L.qb);
         qlo = reinterpret_cast<float*>(smem + L.qlo);
         qhi = reinterpret_cast<float*>(smem + L.qhi);
         qD = reinterpret_cast<double*>(smem + L.qD);
+        qkey = reinterpret_cast<uint64_t*>(smem + L.qkey);
         qg = reinterpret_cast<uint64_t*>(smem + L.qg);
+        fw = reinterpret_cast<float*>(smem + L.fw);
         order = reinterpret_cast<uint32_t*>(smem + L.order);
         acc = reinterpret_cast<uint32_t*>(smem + L.acc);
         bitmap = reinterpret_cast<uint32_t*>(smem + L.bitmap);
@@ -287,6 +314,9 @@ struct ChainCtx {
     double thr;
     uint32_t seed_lo, seed_hi;
     bool use_filter;
+    float rel;   // (E + 4) 2^-23: relative part of the FP32 key bound
+    bool pos_thr;            // threshold > 0
+    float thr_lo, thr_hi;    // binary32 neighbours of the threshold
 };
 
 // ---- set-up: species (validated against S), counts, coefficients, shell vectors ----------------
@@ -302,6 +332,13 @@ __device__ void chain_setup(const ChainDesc& d, ChainSmem& m, ChainShared& sh, C
     c.thr = d.threshold;
     c.seed_lo = (uint32_t)(d.seed & 0xFFFFFFFFu);
     c.seed_hi = (uint32_t)(d.seed >> 32);
+    c.rel = (float)(c.E + 4) * kTwoUlp;
+    c.pos_thr = d.threshold > 0.0;
+    {
+        float f = (float)d.threshold;
+        c.thr_lo = ((double)f > d.threshold) ? nextafterf(f, -CUDART_INF_F) : f;
+        c.thr_hi = ((double)f < d.threshold) ? nextafterf(f, CUDART_INF_F) : f;
+    }
     const ShellTable& TAB = c_shells[KIND];
     c.ztot = TAB.first[c.M];
     const int S = c.S, E = c.E;
@@ -331,6 +368,10 @@ __device__ void chain_setup(const ChainDesc& d, ChainSmem& m, ChainShared& sh, C
             m.types[i] = (uint8_t)((v0 & 0xF) | ((v1 & 0xF) << 4));
         }
     }
+    {
+        const int P = 4 * S - 4;   // entries a swap touches per shell
+        for (int f = tid; f < c.M * P; f += T) m.slot[f] = (uint16_t)(((f / P) << 8) | (f % P));
+    }
     for (int v = tid; v < c.ztot; v += T)
         m.vec[v] = (uint32_t)(uint8_t)TAB.v[v][0] | ((uint32_t)(uint8_t)TAB.v[v][1] << 8) |
                    ((uint32_t)(uint8_t)TAB.v[v][2] << 16);
@@ -352,9 +393,11 @@ __device__ void chain_setup(const ChainDesc& d, ChainSmem& m, ChainShared& sh, C
         m.fa[e] = (float)a;
         m.fb[e] = (float)b;
         m.fQ[e] = (float)Q;
-        m.ft[e] = (float)t;
-        const float nq = (float)n * (float)Q;
-        m.beta[e] = beta_of((float)w, (float)Q, nq, (float)t, (1.0f - nq) - (float)t);
+        m.fw[e] = (float)w;
+        m.fe0[e] = (float)err;
+        m.dn[e] = 0;
+        m.tiny[e] = (float)(2.0 * w * Q * 1.4210854715202004e-14 * (4.0 + 2.0 * (double)d.N / (double)d.n_per[j] + 2.0 * fabs(t)));
+        m.beta[e] = fmaf(kTwoUlp, fabsf(m.fb[e]), m.tiny[e]);
         // The FP32 estimate needs every |a| dN^2 and |b| dN to stay far inside the float range;
         // |e| <= 1 + N / N_j + |t| bounds b over the whole search.
         const double zz = 2.0 * TAB.z[k];
@@ -401,11 +444,11 @@ __device__ float score_range(const ChainDesc& d, ChainSmem& m, ChainShared& sh, 
         float lo = -CUDART_INF_F, hi = CUDART_INF_F;
         if (c.use_filter) {
             float Dt, err;
-            score_float(M, c.S, m.fa, m.fb, A, B, gb, Dt, err);
+            score_float(M, c.S, m.fa, m.fb, A, B, gb, c.rel, Dt, err);
             hi = __fadd_ru(Dt, err);
             lo = __fadd_rd(Dt, -err);
             my_umin = fminf(my_umin, hi);
-            if ((double)lo > c.thr) continue;   // cannot be accepted
+            if (c.pos_thr ? (lo > c.thr_hi) : (lo >= 0.f)) continue;   // cannot be accepted
         }
         const int slot = atomicAdd(&sh.qn, 1);
         m.qk[slot] = kk;
@@ -506,8 +549,8 @@ __device__ void apply_slot(const ChainDesc& d, ChainSmem& m, ChainShared& sh, co
         const double bcoef = __dmul_rn(-2.0, __dmul_rn(d.w[k], __dmul_rn(m.Q[e], err)));
         m.cb[e] = bcoef;
         m.fb[e] = (float)bcoef;
-        const float nq = (float)n * m.fQ[e];
-        m.beta[e] = beta_of((float)d.w[k], m.fQ[e], nq, m.ft[e], (1.0f - nq) - m.ft[e]);
+        m.fe0[e] = (float)err;
+        m.beta[e] = fmaf(kTwoUlp, fabsf(m.fb[e]), m.tiny[e]);
     }
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -533,7 +576,7 @@ __device__ void rank_eligible(ChainSmem& m, ChainShared& sh, const ChainCtx& c, 
         const uint32_t a = m.qa[q], b = m.qb[q];
         const int A = load_species<BITS>(m.types, a), B = load_species<BITS>(m.types, b);
         if (a == b || A == B) continue;   // null moves are never accepted
-        int v = eligible_interval(m.qlo[q], m.qhi[q], c.thr);
+        int v = eligible_interval(m.qlo[q], m.qhi[q], c.pos_thr, c.thr_lo, c.thr_hi);
         bool exact = false;
         if (v < 0) {
             m.qD[q] = exact_key(c.M, c.S, m.ca, m.cb, A, B, m.qg + q * c.M);
@@ -563,7 +606,11 @@ __device__ void rank_eligible(ChainSmem& m, ChainShared& sh, const ChainCtx& c, 
         }
     }
     __syncthreads();
-    for (int s = tid; s < ne; s += T) m.acc[s] &= 0x7FFFFFFFu;
+    for (int s = tid; s < ne; s += T) {
+        const uint32_t q = m.acc[s] & 0x7FFFFFFFu;
+        m.acc[s] = q;
+        m.qkey[q] = order_key(m.qD[q]);
+    }
     __syncthreads();
     int keep = ne;
     if (group_top > 0) {
@@ -572,9 +619,11 @@ __device__ void rank_eligible(ChainSmem& m, ChainShared& sh, const ChainCtx& c, 
             const uint32_t q = m.acc[s];
             const uint32_t grp = m.qk[q] / G;
             int ahead = 0;
+            const uint64_t kq = m.qkey[q];
+            const uint32_t kk = m.qk[q];
             for (int o = 0; o < ne; ++o) {
                 const uint32_t q2 = m.acc[o];
-                if (m.qk[q2] / G == grp && better(m.qD[q2], m.qk[q2], m.qD[q], m.qk[q])) ++ahead;
+                if (m.qk[q2] / G == grp && better_key(m.qkey[q2], m.qk[q2], kq, kk)) ++ahead;
             }
             m.order[s] = (ahead < group_top) ? q : 0xFFFFFFFFu;
         }
@@ -588,24 +637,51 @@ __device__ void rank_eligible(ChainSmem& m, ChainShared& sh, const ChainCtx& c, 
     }
     for (int s = tid; s < keep; s += T) {
         const uint32_t q = m.acc[s];
+        const uint64_t kq = m.qkey[q];
+        const uint32_t kk = m.qk[q];
         int rank = 0;
         for (int o = 0; o < keep; ++o) {
             const uint32_t q2 = m.acc[o];
-            rank += better(m.qD[q2], m.qk[q2], m.qD[q], m.qk[q]) ? 1 : 0;
+            rank += better_key(m.qkey[q2], m.qk[q2], kq, kk) ? 1 : 0;
         }
         m.order[rank] = q;
     }
     __syncthreads();
 }
 
+// The entries a swap of species A and B can change, per shell: row A, row B (S entries each), then
+// columns A and B of the S - 2 other rows.  Slot s of shell k -> entry (k, i, j).
+__device__ __forceinline__ void swap_entry(int S, int A, int B, int s, int& i, int& j) {
+    if (s < S) {
+        i = A;
+        j = s;
+    } else if (s < 2 * S) {
+        i = B;
+        j = s - S;
+    } else {
+        int t = s - 2 * S;
+        if (t >= S - 2) t -= S - 2;
+        const int lo = A < B ? A : B, hi = A < B ? B : A;
+        int r = t;
+        r += (r >= lo) ? 1 : 0;
+        r += (r >= hi) ? 1 : 0;
+        i = r;
+        j = (s < 3 * S - 2) ? A : B;
+    }
+}
+
 // ---- multi-accept walk over m.order[0, ne) by warp 0 (sequential by definition) ----------------
 // Each re-check against the running counts is an FP32 estimate over the lanes with a rigorous
-// bound; the exact binary64 key is computed only when the bound cannot decide eligibility.
+// bound (the FP32 bound above plus beta for the running coefficients); the exact binary64 key is
+// computed only when the bound cannot decide eligibility.
 template <int KIND, int BITS>
-__device__ void walk(const ChainDesc& d, ChainSmem& m, ChainShared& sh, const ChainCtx& c, int ne) {
+__device__ void walk_bitmap(const ChainDesc& d, ChainSmem& m, ChainShared& sh, const ChainCtx& c, int ne) {
     const int lane = threadIdx.x & 31;
+    for (uint32_t i = threadIdx.x; i < (c.N + 31) / 32; i += blockDim.x) m.bitmap[i] = 0;
+    __syncthreads();
     if ((threadIdx.x >> 5) == 0) {
-        const int S = c.S, M = c.M, E = c.E;
+        const int S = c.S, M = c.M, SS = S * S;
+        const int P = 4 * S - 4;   // entries a swap touches per shell
         int n_acc = 0;
         for (int r = 0; r < ne; ++r) {
             if (d.max_accept > 0 && n_acc >= d.max_accept) break;
@@ -617,24 +693,26 @@ __device__ void walk(const ChainDesc& d, ChainSmem& m, ChainShared& sh, const Ch
             const uint64_t* gq = m.qg + q * M;
             bool take = true;   // before the first accept the running state is the step-start state
             if (n_acc > 0) {
-                float acc = 0.f, mag = 0.f, bet = 0.f;
-                for (int e = lane; e < E; e += 32) {
-                    const int k = e / (S * S), i = (e / S) % S, j = e % S;
+                float acc = 0.f, err = 0.f;
+                for (int f = lane; f < M * P; f += 32) {
+                    const int v = m.slot[f], k = v >> 8;
+                    int i, j;
+                    swap_entry(S, A, B, v & 0xFF, i, j);
                     const int dl = entry_delta(gq[k], A, B, i, j);
                     if (dl == 0) continue;
+                    const int e = k * SS + i * S + j;
                     const float x = (float)dl, ax = fabsf(x);
                     acc = fmaf(x, fmaf(m.fa[e], x, m.fb[e]), acc);
-                    mag = fmaf(ax, fmaf(fabsf(m.fa[e]), ax, fabsf(m.fb[e])), mag);
-                    bet = fmaf(ax, m.beta[e], bet);
+                    err = fmaf(ax, fmaf(c.rel * fabsf(m.fa[e]), ax, fmaf(c.rel, fabsf(m.fb[e]), m.beta[e])), err);
                 }
 #pragma unroll
                 for (int o = 16; o > 0; o >>= 1) {
                     acc += __shfl_xor_sync(0xFFFFFFFFu, acc, o);
-                    mag += __shfl_xor_sync(0xFFFFFFFFu, mag, o);
-                    bet += __shfl_xor_sync(0xFFFFFFFFu, bet, o);
+                    err += __shfl_xor_sync(0xFFFFFFFFu, err, o);
                 }
-                const float err = fmaf(mag, kRelBound, bet + kAbsBound);
-                int verdict = eligible_interval(__fadd_rd(acc, -err), __fadd_ru(acc, err), c.thr);
+                // A few extra relative ulps cover the rounding of the lane sums.
+                err = fmaf(err, 1.0f + 64.0f * kTwoUlp, kAbsBound);
+                int verdict = eligible_interval(__fadd_rd(acc, -err), __fadd_ru(acc, err), c.pos_thr, c.thr_lo, c.thr_hi);
                 if (verdict < 0) {
                     double Dp = 0.0;
                     if (lane == 0) Dp = exact_key_running(M, S, m.cnt, m.Q, m.tgt, m.ca, d.w, A, B, gq);
@@ -645,13 +723,16 @@ __device__ void walk(const ChainDesc& d, ChainSmem& m, ChainShared& sh, const Ch
             }
             if (!take) continue;
             __syncwarp();
-            for (int e = lane; e < E; e += 32) {
-                const int k = e / (S * S), i = (e / S) % S, j = e % S;
+            for (int f = lane; f < M * P; f += 32) {
+                const int v = m.slot[f], k = v >> 8;
+                int i, j;
+                swap_entry(S, A, B, v & 0xFF, i, j);
                 const int dl = entry_delta(gq[k], A, B, i, j);
                 if (dl == 0) continue;
-                const int n = m.cnt[e] + dl;
-                m.cnt[e] = n;
-                float_coefficient(e, n, (float)d.w[k], m.fQ, m.ft, m.fb, m.beta);
+                const int e = k * SS + i * S + j;
+                m.cnt[e] += dl;
+                m.dn[e] += dl;
+                running_coefficient(e, m.dn[e], (float)d.w[k], m.fQ, m.fe0, m.tiny, m.fb, m.beta);
             }
             mark_neighbourhood<KIND, true>(c.g, a, c.ztot, lane, 32, m.vec, m.bitmap);
             mark_neighbourhood<KIND, true>(c.g, b, c.ztot, lane, 32, m.vec, m.bitmap);
@@ -668,16 +749,184 @@ __device__ void walk(const ChainDesc& d, ChainSmem& m, ChainShared& sh, const Ch
     __syncthreads();
 }
 
-// After a walk: clear the bitmap around the swapped sites and refresh the binary64 coefficients
-// (and their FP32 roundings used by the next step's estimates) from the updated counts.
+// ---- multi-accept walk, pairwise form (ranked list of at most d.pair_cap candidates) ----------
+// Prepared in parallel: every candidate's nonzero count changes (entry, dN), its sites' positions,
+// and the conflict matrix (candidates i < r conflict when a site of one lies in the closed shell
+// neighbourhood of a site of the other: the minimum-image squared distance is at most r2 of
+// shell M, which for cells of at least two conventional cells per axis is the same relation).
+// Warp 0 then walks the list: conflicts are one AND with the accepted set, re-checks read the
+// prepared lists, and no site bitmap is needed.
+struct PairWalk {
+    uint16_t* list;    // [ne][MP]: entry | (dN & 0xFF) << 8
+    uint8_t* nlist;    // [ne]
+    int16_t* pos;      // [ne][6]: X, Y, Z of a, then of b
+    uint32_t* conf;    // [ne][nw]
+    uint32_t* site;    // [ne][2]: a, b
+    uint8_t* spec;     // [ne][2]: species of a and of b
+};
+
+__device__ __forceinline__ PairWalk pair_walk_arrays(uint32_t* base, int pair_cap, int M, int S) {
+    const uint32_t mp = (uint32_t)(M * (4 * S - 4));
+    const uint32_t nw = (uint32_t)((pair_cap + 31) / 32);
+    uint8_t* p = reinterpret_cast<uint8_t*>(base);
+    PairWalk w;
+    w.list = reinterpret_cast<uint16_t*>(p);
+    p += align_up((uint32_t)pair_cap * 2 * mp, 16);
+    w.nlist = p;
+    p += align_up((uint32_t)pair_cap, 16);
+    w.pos = reinterpret_cast<int16_t*>(p);
+    p += align_up((uint32_t)pair_cap * 12, 16);
+    w.conf = reinterpret_cast<uint32_t*>(p);
+    p += align_up((uint32_t)pair_cap * 4 * nw, 16);
+    w.site = reinterpret_cast<uint32_t*>(p);
+    w.spec = p + (size_t)pair_cap * 8;
+    return w;
+}
+
+__device__ __forceinline__ int wrap_min_image(int dx, int period) {
+    // dx in (-period, period) -> representative with |dx| <= period / 2
+    if (dx > period / 2) dx -= period;
+    if (dx < -(period / 2)) dx += period;
+    return dx;
+}
+
+template <int KIND, int BITS>
+__device__ void walk_pairs(const ChainDesc& d, ChainSmem& m, ChainShared& sh, const ChainCtx& c, int ne) {
+    const int tid = threadIdx.x, T = blockDim.x, lane = tid & 31;
+    const int S = c.S, M = c.M, SS = S * S, P = 4 * S - 4, MP = M * P;
+    const int nw = (ne + 31) / 32;
+    PairWalk w = pair_walk_arrays(m.bitmap, d.pair_cap, M, S);
+    // 1. Per candidate: its list of nonzero count changes and its sites' positions.
+    for (int r = tid; r < ne; r += T) {
+        const uint32_t q = m.order[r];
+        const uint32_t a = m.qa[q], b = m.qb[q];
+        const int A = load_species<BITS>(m.types, a), B = load_species<BITS>(m.types, b);
+        int n = 0;
+        for (int f = 0; f < MP; ++f) {
+            const int v = m.slot[f], k = v >> 8;
+            int i, j;
+            swap_entry(S, A, B, v & 0xFF, i, j);
+            const int dl = entry_delta(m.qg[q * M + k], A, B, i, j);
+            if (dl == 0) continue;
+            w.list[r * MP + n++] = (uint16_t)((k * SS + i * S + j) | ((dl & 0xFF) << 8));
+        }
+        w.nlist[r] = (uint8_t)n;
+        w.site[2 * r] = a;
+        w.site[2 * r + 1] = b;
+        w.spec[2 * r] = (uint8_t)A;
+        w.spec[2 * r + 1] = (uint8_t)B;
+        int X, Y, Z;
+        site_coords<KIND>(c.g, a, X, Y, Z);
+        w.pos[r * 6 + 0] = (int16_t)X;
+        w.pos[r * 6 + 1] = (int16_t)Y;
+        w.pos[r * 6 + 2] = (int16_t)Z;
+        site_coords<KIND>(c.g, b, X, Y, Z);
+        w.pos[r * 6 + 3] = (int16_t)X;
+        w.pos[r * 6 + 4] = (int16_t)Y;
+        w.pos[r * 6 + 5] = (int16_t)Z;
+    }
+    __syncthreads();
+    // 2. Conflict matrix rows: bit i of row r (i < r) when candidates i and r conflict.
+    const int r2max = c_shells[KIND].radius2[M - 1];
+    const int PX = 2 * c.g.Lx, PY = 2 * c.g.Ly, PZ = 2 * c.g.Lz;
+    for (int t = tid; t < ne * nw; t += T) {
+        const int r = t / nw, wd = t % nw;
+        uint32_t bits = 0;
+        const int i_end = min(r, 32 * wd + 32);
+        for (int i = 32 * wd; i < i_end; ++i) {
+            bool hit = false;
+#pragma unroll
+            for (int u = 0; u < 2; ++u)
+#pragma unroll
+                for (int v = 0; v < 2; ++v) {
+                    const int dx = wrap_min_image(w.pos[r * 6 + 3 * v] - w.pos[i * 6 + 3 * u], PX);
+                    const int dy = wrap_min_image(w.pos[r * 6 + 3 * v + 1] - w.pos[i * 6 + 3 * u + 1], PY);
+                    const int dz = wrap_min_image(w.pos[r * 6 + 3 * v + 2] - w.pos[i * 6 + 3 * u + 2], PZ);
+                    hit |= (dx * dx + dy * dy + dz * dz) <= r2max;
+                }
+            bits |= hit ? (1u << (i - 32 * wd)) : 0u;
+        }
+        w.conf[r * nw + wd] = bits;
+    }
+    __syncthreads();
+    // 3. The walk.
+    if ((tid >> 5) == 0) {
+        uint32_t taken = 0;   // lane l holds bits 32 l .. 32 l + 31 of the accepted set
+        int n_acc = 0;
+        for (int r = 0; r < ne; ++r) {
+            if (d.max_accept > 0 && n_acc >= d.max_accept) break;
+            const bool hit = (lane < nw) && ((w.conf[r * nw + lane] & taken) != 0u);
+            if (__any_sync(0xFFFFFFFFu, hit)) continue;
+            const int cnt = w.nlist[r];
+            bool take = true;   // before the first accept the running state is the step-start state
+            if (n_acc > 0) {
+                float acc = 0.f, err = 0.f;
+                for (int x = lane; x < cnt; x += 32) {
+                    const uint32_t v = w.list[r * MP + x];
+                    const int e = (int)(v & 0xFFu);
+                    const float xf = (float)(int)(int8_t)(v >> 8), ax = fabsf(xf);
+                    acc = fmaf(xf, fmaf(m.fa[e], xf, m.fb[e]), acc);
+                    err = fmaf(ax, fmaf(c.rel * fabsf(m.fa[e]), ax, fmaf(c.rel, fabsf(m.fb[e]), m.beta[e])), err);
+                }
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    acc += __shfl_xor_sync(0xFFFFFFFFu, acc, o);
+                    err += __shfl_xor_sync(0xFFFFFFFFu, err, o);
+                }
+                err = fmaf(err, 1.0f + 64.0f * kTwoUlp, kAbsBound);
+                int verdict =
+                    eligible_interval(__fadd_rd(acc, -err), __fadd_ru(acc, err), c.pos_thr, c.thr_lo, c.thr_hi);
+                if (verdict < 0) {
+                    const uint32_t q = m.order[r];
+                    double Dp = 0.0;
+                    if (lane == 0) {
+                        const int A = load_species<BITS>(m.types, m.qa[q]), B = load_species<BITS>(m.types, m.qb[q]);
+                        Dp = exact_key_running(M, S, m.cnt, m.Q, m.tgt, m.ca, d.w, A, B, m.qg + q * M);
+                    }
+                    Dp = __shfl_sync(0xFFFFFFFFu, Dp, 0);
+                    verdict = eligible(Dp, false, c.thr) ? 1 : 0;
+                }
+                take = verdict == 1;
+            }
+            if (!take) continue;
+            __syncwarp();
+            for (int x = lane; x < cnt; x += 32) {
+                const uint32_t v = w.list[r * MP + x];
+                const int e = (int)(v & 0xFFu), dl = (int)(int8_t)(v >> 8);
+                m.cnt[e] += dl;
+                const int dn = m.dn[e] + dl;
+                m.dn[e] = dn;
+                running_coefficient(e, dn, m.fw[e], m.fQ, m.fe0, m.tiny, m.fb, m.beta);
+            }
+            if (lane == (r >> 5)) taken |= 1u << (r & 31);
+            if (lane == 0) {
+                const uint32_t a = w.site[2 * r], b = w.site[2 * r + 1];
+                store_species<BITS>(m.types, a, w.spec[2 * r + 1]);
+                store_species<BITS>(m.types, b, w.spec[2 * r]);
+                m.acc[n_acc] = m.order[r];
+            }
+            ++n_acc;
+            __syncwarp();
+        }
+        if (lane == 0) sh.n_acc = n_acc;
+    }
+    __syncthreads();
+}
+
+// Multi-accept walk over the ranked list m.order[0, ne).
+template <int KIND, int BITS>
+__device__ void walk(const ChainDesc& d, ChainSmem& m, ChainShared& sh, const ChainCtx& c, int ne) {
+    if (ne <= d.pair_cap)
+        walk_pairs<KIND, BITS>(d, m, sh, c, ne);
+    else
+        walk_bitmap<KIND, BITS>(d, m, sh, c, ne);
+}
+
+// After a walk: refresh the binary64 coefficients (and their FP32 roundings used by the next
+// step's estimates) from the updated counts.
 template <int KIND>
 __device__ void after_walk(const ChainDesc& d, ChainSmem& m, ChainShared& sh, const ChainCtx& c) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const int na = sh.n_acc;
-    for (int x = warp; x < 2 * na; x += nw) {
-        const uint32_t q = m.acc[x >> 1];
-        mark_neighbourhood<KIND, false>(c.g, (x & 1) ? m.qb[q] : m.qa[q], c.ztot, lane, 32, m.vec, m.bitmap);
-    }
     if (na > 0) {
         const int S = c.S;
         for (int e = threadIdx.x; e < c.E; e += blockDim.x) {
@@ -686,6 +935,9 @@ __device__ void after_walk(const ChainDesc& d, ChainSmem& m, ChainShared& sh, co
             const double b = __dmul_rn(-2.0, __dmul_rn(d.w[k], __dmul_rn(m.Q[e], err)));
             m.cb[e] = b;
             m.fb[e] = (float)b;
+            m.fe0[e] = (float)err;
+            m.dn[e] = 0;
+            m.beta[e] = fmaf(kTwoUlp, fabsf(m.fb[e]), m.tiny[e]);
         }
     }
     __syncthreads();
@@ -753,7 +1005,7 @@ __device__ __forceinline__ void report_invalid(const ChainDesc& d) {
 // ------------------------------------------------------------------------------------------------
 template <int KIND, int BITS>
 __device__ void run_chain(const ChainDesc& d, uint8_t* smem, ChainShared& sh) {
-    const ChainLayout L = chain_layout(d.N, d.M, d.S, d.qcap, BITS, d.accept_mode);
+    const ChainLayout L = chain_layout(d.N, d.M, d.S, d.qcap, BITS, d.accept_mode, d.pair_cap);
     ChainSmem m(smem, L);
     ChainCtx c;
     chain_setup<KIND, BITS>(d, m, sh, c);
@@ -830,7 +1082,7 @@ static __device__ bool grid_barrier(CoopHeader* h, unsigned long long target, Ch
 
 template <int KIND, int BITS>
 __device__ void run_coop_chain(const ChainDesc& d, uint8_t* smem, ChainShared& sh) {
-    const ChainLayout L = chain_layout(d.N, d.M, d.S, d.qcap, BITS, d.accept_mode);
+    const ChainLayout L = chain_layout(d.N, d.M, d.S, d.qcap, BITS, d.accept_mode, d.pair_cap);
     ChainSmem m(smem, L);
     ChainCtx c;
     chain_setup<KIND, BITS>(d, m, sh, c);

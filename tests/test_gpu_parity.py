@@ -201,6 +201,7 @@ def test_search_best_of_k_bit_exact(kind, L, M, S, K, steps, seed):
     (FCC, (6, 6, 6), 3, 4, 256, 30, 0, 1), (BCC, (9, 9, 9), 2, 5, 512, 20, 0, 2),
     (FCC, (3, 3, 3), 5, 3, 64, 60, 0, 3), (BCC, (10, 10, 10), 3, 6, 256, 25, 5, 4),
     (FCC, (10, 10, 10), 3, 4, 1024, 10, 0, 5),
+    (BCC, (16, 16, 16), 2, 4, 2048, 3, 0, 6),     # ranked lists longer than the pairwise walk holds
 ])
 def test_search_multi_accept_bit_exact(kind, L, M, S, K, steps, max_acc, seed):
     N = oracle.num_sites(kind, L)
