@@ -42,6 +42,24 @@ def env_rank():
         int(os.environ.get("LOCAL_RANK", "0"))
 
 
+def replica_seed(rank):
+    """Each rank runs an independent chain (replicas: no data-path collective)."""
+    return 1 + rank
+
+
+def aggregate_ranks(dist, total_ms, search_ms, trials_local, device):
+    """Max over ranks of the timed device time (and of the search part); whole-job throughput =
+    the trials of all ranks over that time.  dist = None for a single process."""
+    import torch
+    t = torch.tensor([total_ms, search_ms], dtype=torch.float64, device=device)
+    n = torch.tensor([float(trials_local)], dtype=torch.float64, device=device)
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(n, op=dist.ReduceOp.SUM)
+    total_ms, search_ms = float(t[0]), float(t[1])
+    return total_ms, search_ms, float(n[0]) / (total_ms / 1000.0)
+
+
 def load_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -145,7 +163,7 @@ def run_ours(args):
     f2 = torch.empty(1, dtype=torch.float64, device="cuda")
     result = torch.zeros(hea.RESULT_BYTES, dtype=torch.uint8, device="cuda")
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
-    seed = 1 + rank
+    seed = replica_seed(rank)
 
     def one_step(step_seed):
         hea.hea_init_config(lat, spec.n_per, step_seed, types, stream)
@@ -190,12 +208,8 @@ def run_ours(args):
     if res["status"] != 0:
         raise RuntimeError(f"search status {res['status']}")
     # Max over ranks of the timed device time.
-    t_local = torch.tensor([total_ms, float(sum(search_ms))], dtype=torch.float64, device="cuda")
-    if world > 1:
-        dist.all_reduce(t_local, op=dist.ReduceOp.MAX)
-    total_ms, search_total_ms = [float(x) for x in t_local.cpu()]
-    trials_all = trials_per_step * args.steps * world
-    value = trials_all / (total_ms / 1000.0)
+    total_ms, search_total_ms, value = aggregate_ranks(dist if world > 1 else None, total_ms, float(sum(search_ms)),
+                                                        trials_per_step * args.steps, "cuda")
 
     # End to end through the public API with host buffers: initial structure copied in from pinned
     # memory, recount, alpha, search, final structure + counts + result copied back.

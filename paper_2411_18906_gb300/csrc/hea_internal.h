@@ -49,12 +49,17 @@ __host__ __device__ inline uint32_t align_up(uint32_t x, uint32_t a) { return (x
 
 // Bytes of the pairwise-walk data for a ranked list of up to n candidates: per candidate its
 // nonzero count changes (2 bytes each, M (4S - 4) at most), its count, its two sites' coordinates
-// (6 int16) and its row of the conflict matrix (ceil(n / 32) words).
+// (6 int16), its row of the conflict matrix (ceil(n / 32) words) and its sites and species; then
+// the scratch of one batch of 32 candidates.
 __host__ __device__ inline uint32_t pair_walk_bytes(int n, int M, int S) {
     const uint32_t mp = (uint32_t)(M * (4 * S - 4));
     const uint32_t nw = (uint32_t)((n + 31) / 32);
+    const uint32_t E = (uint32_t)(M * S * S);
     return align_up((uint32_t)n * 2 * mp, 16) + align_up((uint32_t)n, 16) + align_up((uint32_t)n * 12, 16) +
-           align_up((uint32_t)n * 4 * nw, 16) + align_up((uint32_t)n * 10, 16);
+           align_up((uint32_t)n * 4 * nw, 16) + align_up((uint32_t)n * 10, 16) +
+           // batch scratch of the walk: dense count changes (int8 [32][E]), cross terms and their
+           // bounds (float [32][32] each), estimates and their bounds (float [32] each)
+           align_up(32 * E, 16) + 2 * 32 * 32 * 4 + 2 * 32 * 4;
 }
 
 // qcap: candidate slots (the candidates a CTA scores per step, or the merged records of a

@@ -46,6 +46,8 @@ struct ChainShared {
     int status;
     int win_q;       // best-of-K: slot of the winner (-1 none)
     int sync_ok;
+    int batch_n;     // walk: accepted candidates of the current batch
+    int walk_done;   // walk: max_accept reached
     float umin;      // min over candidates of the upper bound on D
     int64_t steps;
     int64_t accepted;
@@ -763,6 +765,11 @@ struct PairWalk {
     uint32_t* conf;    // [ne][nw]
     uint32_t* site;    // [ne][2]: a, b
     uint8_t* spec;     // [ne][2]: species of a and of b
+    int8_t* dense;     // [32][E]: count changes of the batch's candidates
+    float* X;          // [32][32]: cross terms sum_e a_e dN_i dN_j of the batch (i < j)
+    float* Xe;         // [32][32]: their bounds
+    float* bD;         // [32]: re-check estimates at the start of the batch
+    float* bE;         // [32]: their bounds
 };
 
 __device__ __forceinline__ PairWalk pair_walk_arrays(uint32_t* base, int pair_cap, int M, int S) {
@@ -780,7 +787,56 @@ __device__ __forceinline__ PairWalk pair_walk_arrays(uint32_t* base, int pair_ca
     p += align_up((uint32_t)pair_cap * 4 * nw, 16);
     w.site = reinterpret_cast<uint32_t*>(p);
     w.spec = p + (size_t)pair_cap * 8;
+    p += align_up((uint32_t)pair_cap * 10, 16);
+    w.dense = reinterpret_cast<int8_t*>(p);
+    p += align_up(32u * (uint32_t)(M * S * S), 16);
+    w.X = reinterpret_cast<float*>(p);
+    w.Xe = w.X + 32 * 32;
+    w.bD = w.Xe + 32 * 32;
+    w.bE = w.bD + 32;
     return w;
+}
+
+// Exact key against the running counts when some accepted swaps of the current batch are not yet
+// applied: count of entry e = cnt[e] + sum of the pending candidates' changes (dense rows).
+static __device__ double exact_key_pending(int M, int S, const int32_t* cnt, const double* Q, const double* tgt,
+                                           const double* ca, const double* w, int A, int B, const uint64_t* gb,
+                                           const int8_t* dense, int E, const int* pend, int npend) {
+    double D = 0.0;
+    for (int k = 0; k < M; ++k) {
+        const uint64_t g_k = gb[k];
+        for (int i = 0; i < S; ++i) {
+            const bool row = (i == A || i == B);
+            for (int j = 0; j < S; ++j) {
+                if (!row && j != A && j != B) continue;
+                const int dl = entry_delta(g_k, A, B, i, j);
+                if (dl == 0) continue;
+                const int e = (k * S + i) * S + j;
+                int n = cnt[e];
+                for (int p = 0; p < npend; ++p) n += dense[pend[p] * E + e];
+                const double err = __dsub_rn(__dsub_rn(1.0, __dmul_rn((double)n, Q[e])), tgt[e]);
+                const double b = __dmul_rn(-2.0, __dmul_rn(w[k], __dmul_rn(Q[e], err)));
+                const double x = (double)dl;
+                D = __fma_rn(x, __fma_rn(ca[e], x, b), D);
+            }
+        }
+    }
+    return D;
+}
+
+// Replaces the nibble (4-bit storage) or byte of site i; safe against other threads writing other
+// sites of the same word.
+template <int BITS>
+__device__ __forceinline__ void store_species_atomic(uint8_t* s, uint32_t i, int v) {
+    if (BITS == 8) {
+        s[i] = (uint8_t)v;
+    } else {
+        const uint32_t byte = i >> 1;
+        uint32_t* word = reinterpret_cast<uint32_t*>(s + (byte & ~3u));
+        const uint32_t sh = (byte & 3u) * 8 + (i & 1u) * 4;
+        atomicAnd(word, ~(0xFu << sh));
+        atomicOr(word, (uint32_t)v << sh);
+    }
 }
 
 __device__ __forceinline__ int wrap_min_image(int dx, int period) {
@@ -849,17 +905,39 @@ __device__ void walk_pairs(const ChainDesc& d, ChainSmem& m, ChainShared& sh, co
         w.conf[r * nw + wd] = bits;
     }
     __syncthreads();
-    // 3. The walk.
-    if ((tid >> 5) == 0) {
-        uint32_t taken = 0;   // lane l holds bits 32 l .. 32 l + 31 of the accepted set
-        int n_acc = 0;
-        for (int r = 0; r < ne; ++r) {
-            if (d.max_accept > 0 && n_acc >= d.max_accept) break;
-            const bool hit = (lane < nw) && ((w.conf[r * nw + lane] & taken) != 0u);
-            if (__any_sync(0xFFFFFFFFu, hit)) continue;
-            const int cnt = w.nlist[r];
-            bool take = true;   // before the first accept the running state is the step-start state
-            if (n_acc > 0) {
+    // 3. The walk, in batches of up to 32 ranked candidates.  For each batch, in parallel: the dense
+    // count changes of its candidates, their re-check estimates against the running state at the
+    // start of the batch (one warp per candidate), and the cross terms X(i, j) = sum_e a_e dN_i dN_j.
+    // Accepting candidate i changes every coefficient b_e by 2 a_e dN_i (exact algebra), so the key
+    // of a later candidate j moves by exactly 2 X(i, j): warp 0 then decides the batch in order with
+    // scalar corrections, each decision on an interval whose bound covers the estimate, the cross
+    // terms and their roundings (the exact binary64 key when it cannot decide).  The accepted swaps
+    // are applied to counts, species and FP32 coefficients in parallel at the end of the batch.
+    const int E = c.E, warp = tid >> 5, nwarps = T >> 5;
+    uint32_t taken = 0;   // warp 0: lane l holds bits 32 l .. 32 l + 31 of the accepted set
+    if (tid == 0) {
+        sh.n_acc = 0;
+        sh.walk_done = 0;
+    }
+    __syncthreads();
+    for (int r0 = 0; r0 < ne; r0 += 32) {
+        if (sh.walk_done) break;
+        const int nb = min(32, ne - r0);
+        const int acc_before = sh.n_acc;
+        // P1: dense count changes of the batch.
+        for (int x = tid; x < nb * E; x += T) w.dense[x] = 0;
+        __syncthreads();
+        for (int x = tid; x < nb * MP; x += T) {
+            const int j = x / MP, f = x - j * MP;
+            if (f < w.nlist[r0 + j]) {
+                const uint32_t v = w.list[(r0 + j) * MP + f];
+                w.dense[j * E + (int)(v & 0xFFu)] = (int8_t)(v >> 8);
+            }
+        }
+        // P2: re-check estimates at the start of the batch.
+        {
+            for (int j = warp; j < nb; j += nwarps) {
+                const int r = r0 + j, cnt = w.nlist[r];
                 float acc = 0.f, err = 0.f;
                 for (int x = lane; x < cnt; x += 32) {
                     const uint32_t v = w.list[r * MP + x];
@@ -873,44 +951,105 @@ __device__ void walk_pairs(const ChainDesc& d, ChainSmem& m, ChainShared& sh, co
                     acc += __shfl_xor_sync(0xFFFFFFFFu, acc, o);
                     err += __shfl_xor_sync(0xFFFFFFFFu, err, o);
                 }
-                err = fmaf(err, 1.0f + 64.0f * kTwoUlp, kAbsBound);
-                int verdict =
-                    eligible_interval(__fadd_rd(acc, -err), __fadd_ru(acc, err), c.pos_thr, c.thr_lo, c.thr_hi);
-                if (verdict < 0) {
-                    const uint32_t q = m.order[r];
-                    double Dp = 0.0;
-                    if (lane == 0) {
-                        const int A = load_species<BITS>(m.types, m.qa[q]), B = load_species<BITS>(m.types, m.qb[q]);
-                        Dp = exact_key_running(M, S, m.cnt, m.Q, m.tgt, m.ca, d.w, A, B, m.qg + q * M);
-                    }
-                    Dp = __shfl_sync(0xFFFFFFFFu, Dp, 0);
-                    verdict = eligible(Dp, false, c.thr) ? 1 : 0;
+                if (lane == 0) {
+                    w.bD[j] = acc;
+                    w.bE[j] = fmaf(err, 1.0f + 64.0f * kTwoUlp, kAbsBound);
                 }
-                take = verdict == 1;
             }
-            if (!take) continue;
-            __syncwarp();
-            for (int x = lane; x < cnt; x += 32) {
-                const uint32_t v = w.list[r * MP + x];
-                const int e = (int)(v & 0xFFu), dl = (int)(int8_t)(v >> 8);
-                m.cnt[e] += dl;
-                const int dn = m.dn[e] + dl;
-                m.dn[e] = dn;
-                running_coefficient(e, dn, m.fw[e], m.fQ, m.fe0, m.tiny, m.fb, m.beta);
-            }
-            if (lane == (r >> 5)) taken |= 1u << (r & 31);
-            if (lane == 0) {
-                const uint32_t a = w.site[2 * r], b = w.site[2 * r + 1];
-                store_species<BITS>(m.types, a, w.spec[2 * r + 1]);
-                store_species<BITS>(m.types, b, w.spec[2 * r]);
-                m.acc[n_acc] = m.order[r];
-            }
-            ++n_acc;
-            __syncwarp();
         }
-        if (lane == 0) sh.n_acc = n_acc;
+        __syncthreads();
+        // P3: cross terms of the batch, X(i, j) for i < j, with bounds (n_i + 4) 2^-23 sum |a dN_i dN_j|.
+        for (int x = tid; x < 32 * 32; x += T) {
+            const int i = x >> 5, j = x & 31;
+            if (i >= j || j >= nb) continue;
+            const int r = r0 + i, cnt = w.nlist[r];
+            float X = 0.f, mag = 0.f;
+            for (int y = 0; y < cnt; ++y) {
+                const uint32_t v = w.list[r * MP + y];
+                const int e = (int)(v & 0xFFu);
+                const int dj = w.dense[j * E + e];
+                if (dj == 0) continue;
+                const float p = (float)((int)(int8_t)(v >> 8) * dj);
+                X = fmaf(m.fa[e], p, X);
+                mag = fmaf(fabsf(m.fa[e]), fabsf(p), mag);
+            }
+            w.X[i * 32 + j] = X;
+            w.Xe[i * 32 + j] = fmaf(mag, (float)(cnt + 4) * kTwoUlp, kAbsBound);
+        }
+        __syncthreads();
+        // P4: decisions, in order, by warp 0.
+        if (warp == 0) {
+            float corr = 0.f, corrE = 0.f;   // lane j: sum of X(i, j) over accepted i of this batch, and bound
+            int n_acc = acc_before, nbacc = 0;
+            for (int j = 0; j < nb; ++j) {
+                if (d.max_accept > 0 && n_acc >= d.max_accept) {
+                    if (lane == 0) sh.walk_done = 1;
+                    break;
+                }
+                const int r = r0 + j;
+                const bool hit = (lane < nw) && ((w.conf[r * nw + lane] & taken) != 0u);
+                if (__any_sync(0xFFFFFFFFu, hit)) continue;
+                int verdict = 1;   // before the first accept of the step the state is the step-start state
+                if (n_acc > 0) {
+                    if (lane == j) {
+                        const float D0 = w.bD[j], E0 = w.bE[j];
+                        const float v = fmaf(2.0f, corr, D0);
+                        const float er = fmaf(fmaf(2.0f, corrE, E0), 1.0f + 2.0f * 64.0f * kTwoUlp,
+                                              fmaf(2.0f * kTwoUlp, fabsf(D0) + 2.0f * fabsf(corr), kAbsBound));
+                        verdict = eligible_interval(__fadd_rd(v, -er), __fadd_ru(v, er), c.pos_thr, c.thr_lo, c.thr_hi);
+                    }
+                    verdict = __shfl_sync(0xFFFFFFFFu, verdict, j);
+                    if (verdict < 0) {
+                        double Dp = 0.0;
+                        if (lane == 0) {
+                            const uint32_t q = m.order[r];
+                            Dp = exact_key_pending(M, S, m.cnt, m.Q, m.tgt, m.ca, d.w, w.spec[2 * r],
+                                                   w.spec[2 * r + 1], m.qg + q * M, w.dense, E, sh.red_q, nbacc);
+                        }
+                        Dp = __shfl_sync(0xFFFFFFFFu, Dp, 0);
+                        verdict = eligible(Dp, false, c.thr) ? 1 : 0;
+                    }
+                }
+                if (verdict != 1) continue;
+                if (lane == (r >> 5)) taken |= 1u << (r & 31);
+                if (lane == 0) sh.red_q[nbacc] = j;
+                if (lane > j && lane < nb) {
+                    corr += w.X[j * 32 + lane];
+                    corrE += w.Xe[j * 32 + lane] + kTwoUlp * fabsf(corr);
+                }
+                ++nbacc;
+                ++n_acc;
+                __syncwarp();
+            }
+            if (lane == 0) {
+                sh.batch_n = nbacc;
+                sh.n_acc = n_acc;
+            }
+        }
+        __syncthreads();
+        // P5: apply the batch's accepted swaps.
+        const int nba = sh.batch_n;
+        for (int x = tid; x < nba * MP; x += T) {
+            const int r = r0 + sh.red_q[x / MP], f = x % MP;
+            if (f >= w.nlist[r]) continue;
+            const uint32_t v = w.list[r * MP + f];
+            const int e = (int)(v & 0xFFu), dl = (int)(int8_t)(v >> 8);
+            atomicAdd(&m.cnt[e], dl);
+            atomicAdd(&m.dn[e], dl);
+        }
+        for (int x = tid; x < nba; x += T) {
+            const int r = r0 + sh.red_q[x];
+            store_species_atomic<BITS>(m.types, w.site[2 * r], w.spec[2 * r + 1]);
+            store_species_atomic<BITS>(m.types, w.site[2 * r + 1], w.spec[2 * r]);
+            m.acc[acc_before + x] = m.order[r];
+        }
+        __syncthreads();
+        // P6: running FP32 coefficients of every entry (an entry whose change returned to 0 needs
+        // its coefficient back too).
+        if (nba > 0)
+            for (int e = tid; e < E; e += T) running_coefficient(e, m.dn[e], m.fw[e], m.fQ, m.fe0, m.tiny, m.fb, m.beta);
+        __syncthreads();
     }
-    __syncthreads();
 }
 
 // Multi-accept walk over the ranked list m.order[0, ne).

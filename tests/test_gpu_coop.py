@@ -42,6 +42,7 @@ def test_coop_best_of_k_bit_exact(kind, L, M, S, ctas, Kc, steps):
 @pytest.mark.parametrize("kind,L,M,S,ctas,Kc,top,steps", [
     (FCC, (8, 8, 8), 3, 4, 4, 128, 1, 30), (BCC, (10, 10, 10), 2, 5, 8, 64, 2, 30),
     (FCC, (6, 7, 8), 3, 6, 6, 96, 4, 25), (BCC, (6, 6, 6), 3, 4, 2, 256, 3, 25),
+    (FCC, (9, 9, 9), 3, 4, 16, 64, 4, 80),      # long walks over many batches and steps
 ])
 def test_coop_multi_accept_bit_exact(kind, L, M, S, ctas, Kc, top, steps):
     N = oracle.num_sites(kind, L)
