@@ -57,9 +57,10 @@ __host__ __device__ inline uint32_t pair_walk_bytes(int n, int M, int S) {
     const uint32_t E = (uint32_t)(M * S * S);
     return align_up((uint32_t)n * 2 * mp, 16) + align_up((uint32_t)n, 16) + align_up((uint32_t)n * 12, 16) +
            align_up((uint32_t)n * 4 * nw, 16) + align_up((uint32_t)n * 10, 16) +
-           // batch scratch of the walk: dense count changes (int8 [32][E]), cross terms and their
-           // bounds (float [32][32] each), estimates and their bounds (float [32] each)
-           align_up(32 * E, 16) + 2 * 32 * 32 * 4 + 2 * 32 * 4;
+           // batch scratch of the walk: dense count changes (int8 [32][E rounded up to 4]), cross
+           // terms and their bounds (float [32][32] each), estimates, their bounds and the conflict
+           // information of the batch's candidates ([32] each)
+           align_up(32 * ((E + 3) & ~3u), 16) + 2 * 32 * 32 * 4 + 4 * 32 * 4;
 }
 
 // qcap: candidate slots (the candidates a CTA scores per step, or the merged records of a

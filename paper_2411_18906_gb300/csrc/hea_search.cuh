@@ -48,6 +48,7 @@ struct ChainShared {
     int sync_ok;
     int batch_n;     // walk: accepted candidates of the current batch
     int walk_done;   // walk: max_accept reached
+    uint32_t taken[kPairWalkMax / 32];   // walk: accepted set of the ranked list
     float umin;      // min over candidates of the upper bound on D
     int64_t steps;
     int64_t accepted;
@@ -317,6 +318,7 @@ struct ChainCtx {
     uint32_t seed_lo, seed_hi;
     bool use_filter;
     float rel;   // (E + 4) 2^-23: relative part of the FP32 key bound
+    int qcap;    // candidate slots in shared memory
     bool pos_thr;            // threshold > 0
     float thr_lo, thr_hi;    // binary32 neighbours of the threshold
 };
@@ -335,6 +337,7 @@ __device__ void chain_setup(const ChainDesc& d, ChainSmem& m, ChainShared& sh, C
     c.seed_lo = (uint32_t)(d.seed & 0xFFFFFFFFu);
     c.seed_hi = (uint32_t)(d.seed >> 32);
     c.rel = (float)(c.E + 4) * kTwoUlp;
+    c.qcap = d.qcap;
     c.pos_thr = d.threshold > 0.0;
     {
         float f = (float)d.threshold;
@@ -562,6 +565,75 @@ __device__ void apply_slot(const ChainDesc& d, ChainSmem& m, ChainShared& sh, co
     }
 }
 
+// Sorts idx[0, n) ascending under `less` (a strict total order on the indices) with an
+// all-ascending bitonic network (each merge starts with a flip); positions >= n act as +infinity,
+// so n need not be a power of two.  Every thread of the CTA must call it.
+template <typename Less>
+__device__ void block_sort(uint32_t* idx, int n, Less less) {
+    int lg = 0;
+    while ((1 << lg) < n) ++lg;
+    const int P = 1 << lg;
+    for (int ls = 1; ls <= lg; ++ls) {
+        const int size = 1 << ls, half = size >> 1;
+        for (int t = threadIdx.x; t < P / 2; t += blockDim.x) {
+            const int i = ((t >> (ls - 1)) << ls) | (t & (half - 1));
+            const int j = i ^ (size - 1);
+            if (j < n) {
+                const uint32_t a = idx[i], b = idx[j];
+                if (less(b, a)) {
+                    idx[i] = b;
+                    idx[j] = a;
+                }
+            }
+        }
+        __syncthreads();
+        for (int lst = ls - 2; lst >= 0; --lst) {
+            const int stride = 1 << lst;
+            for (int t = threadIdx.x; t < P / 2; t += blockDim.x) {
+                const int i = ((t >> lst) << (lst + 1)) | (t & (stride - 1));
+                const int j = i + stride;
+                if (j < n) {
+                    const uint32_t a = idx[i], b = idx[j];
+                    if (less(b, a)) {
+                        idx[i] = b;
+                        idx[j] = a;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
+}
+
+// Order-preserving compaction of src[0, n) where keep(s) into dst; returns the count (all threads).
+template <typename Keep>
+__device__ int block_compact(const uint32_t* src, int n, uint32_t* dst, Keep keep, ChainShared& sh) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    int base = 0;
+    for (int c0 = 0; c0 < n; c0 += blockDim.x) {
+        const int s = c0 + threadIdx.x;
+        const bool k = (s < n) && keep(s);
+        const uint32_t ball = __ballot_sync(0xFFFFFFFFu, k);
+        if (lane == 0) sh.red_k[warp] = __popc(ball);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int acc = 0;
+            for (int w = 0; w < nw; ++w) {
+                const int cw = (int)sh.red_k[w];
+                sh.red_k[w] = (uint32_t)acc;
+                acc += cw;
+            }
+            sh.red_q[0] = acc;
+        }
+        __syncthreads();
+        const uint32_t v = (s < n) ? src[s] : 0u;
+        if (k) dst[base + (int)sh.red_k[warp] + __popc(ball & ((1u << lane) - 1u))] = v;
+        base += sh.red_q[0];
+        __syncthreads();
+    }
+    return base;
+}
+
 // ---- multi-accept: eligible candidates of slots [0, n) ranked by (D, k) into m.order ------------
 // Eligibility is decided on the interval where it can be and on the exact key otherwise; among the
 // eligible, a candidate gets its exact key when its interval overlaps another one's.  Ranking by
@@ -592,17 +664,32 @@ __device__ void rank_eligible(ChainSmem& m, ChainShared& sh, const ChainCtx& c, 
     }
     __syncthreads();
     const int ne = sh.n_elig;
+    // Overlaps: sorted by lower bound, interval s overlaps another iff the largest upper bound
+    // before it reaches its lower bound or its successor's lower bound is within it.
+    for (int s = tid; s < ne; s += T) m.order[s] = m.acc[s];
+    __syncthreads();
+    block_sort(m.order, ne, [&](uint32_t x, uint32_t y) {
+        const uint32_t qx = x & 0x7FFFFFFFu, qy = y & 0x7FFFFFFFu;
+        return m.qlo[qx] < m.qlo[qy] || (m.qlo[qx] == m.qlo[qy] && qx < qy);
+    });
+    float* pm = reinterpret_cast<float*>(m.qkey);   // prefix maxima of the upper bounds (ping-pong)
+    float* pm2 = pm + c.qcap;
+    for (int s = tid; s < ne; s += T) pm[s] = m.qhi[m.order[s] & 0x7FFFFFFFu];
+    __syncthreads();
+    for (int dd = 1; dd < ne; dd <<= 1) {
+        for (int s = tid; s < ne; s += T) pm2[s] = (s >= dd) ? fmaxf(pm[s], pm[s - dd]) : pm[s];
+        __syncthreads();
+        float* tmp = pm;
+        pm = pm2;
+        pm2 = tmp;
+    }
     for (int s = tid; s < ne; s += T) {
-        if (m.acc[s] & 0x80000000u) continue;
-        const uint32_t q = m.acc[s];
-        const float lo = m.qlo[q], hi = m.qhi[q];
-        bool overlap = false;
-        for (int o = 0; o < ne && !overlap; ++o) {
-            if (o == s) continue;
-            const uint32_t q2 = m.acc[o] & 0x7FFFFFFFu;
-            overlap = (lo <= m.qhi[q2]) && (m.qlo[q2] <= hi);
-        }
-        if (overlap) {
+        const uint32_t x = m.order[s];
+        if (x & 0x80000000u) continue;   // already exact
+        const uint32_t q = x & 0x7FFFFFFFu;
+        const bool before = (s > 0) && (pm[s - 1] >= m.qlo[q]);
+        const bool after = (s + 1 < ne) && (m.qlo[m.order[s + 1] & 0x7FFFFFFFu] <= m.qhi[q]);
+        if (before || after) {
             const int A = load_species<BITS>(m.types, m.qa[q]), B = load_species<BITS>(m.types, m.qb[q]);
             m.qD[q] = exact_key(c.M, c.S, m.ca, m.cb, A, B, m.qg + q * c.M);
         }
@@ -614,40 +701,25 @@ __device__ void rank_eligible(ChainSmem& m, ChainShared& sh, const ChainCtx& c, 
         m.qkey[q] = order_key(m.qD[q]);
     }
     __syncthreads();
+    // Ranking by (group, key, k); the group rule keeps the first group_top of every group.
+    const uint32_t G = (group_top > 0) ? (uint32_t)(group_size > 0 ? group_size : c.K) : 0xFFFFFFFFu;
+    block_sort(m.acc, ne, [&](uint32_t x, uint32_t y) {
+        const uint32_t gx = m.qk[x] / G, gy = m.qk[y] / G;
+        return gx < gy || (gx == gy && better_key(m.qkey[x], m.qk[x], m.qkey[y], m.qk[y]));
+    });
     int keep = ne;
     if (group_top > 0) {
-        const uint32_t G = (uint32_t)(group_size > 0 ? group_size : c.K);
-        for (int s = tid; s < ne; s += T) {
-            const uint32_t q = m.acc[s];
-            const uint32_t grp = m.qk[q] / G;
-            int ahead = 0;
-            const uint64_t kq = m.qkey[q];
-            const uint32_t kk = m.qk[q];
-            for (int o = 0; o < ne; ++o) {
-                const uint32_t q2 = m.acc[o];
-                if (m.qk[q2] / G == grp && better_key(m.qkey[q2], m.qk[q2], kq, kk)) ++ahead;
-            }
-            m.order[s] = (ahead < group_top) ? q : 0xFFFFFFFFu;
-        }
+        keep = block_compact(m.acc, ne, m.order, [&](int s) {
+            return s < group_top || (m.qk[m.acc[s - group_top]] / G != m.qk[m.acc[s]] / G);
+        }, sh);
+        block_sort(m.order, keep, [&](uint32_t x, uint32_t y) {
+            return better_key(m.qkey[x], m.qk[x], m.qkey[y], m.qk[y]);
+        });
+    } else {
+        for (int s = tid; s < ne; s += T) m.order[s] = m.acc[s];
         __syncthreads();
-        if (tid == 0) sh.n_elig = 0;
-        __syncthreads();
-        for (int s = tid; s < ne; s += T)
-            if (m.order[s] != 0xFFFFFFFFu) m.acc[atomicAdd(&sh.n_elig, 1)] = m.order[s];
-        __syncthreads();
-        keep = sh.n_elig;
     }
-    for (int s = tid; s < keep; s += T) {
-        const uint32_t q = m.acc[s];
-        const uint64_t kq = m.qkey[q];
-        const uint32_t kk = m.qk[q];
-        int rank = 0;
-        for (int o = 0; o < keep; ++o) {
-            const uint32_t q2 = m.acc[o];
-            rank += better_key(m.qkey[q2], m.qk[q2], kq, kk) ? 1 : 0;
-        }
-        m.order[rank] = q;
-    }
+    if (tid == 0) sh.n_elig = keep;
     __syncthreads();
 }
 
@@ -765,11 +837,13 @@ struct PairWalk {
     uint32_t* conf;    // [ne][nw]
     uint32_t* site;    // [ne][2]: a, b
     uint8_t* spec;     // [ne][2]: species of a and of b
-    int8_t* dense;     // [32][E]: count changes of the batch's candidates
+    int8_t* dense;     // [32][Ep]: count changes of the batch's candidates (row stride Ep = E rounded up to 4)
     float* X;          // [32][32]: cross terms sum_e a_e dN_i dN_j of the batch (i < j)
     float* Xe;         // [32][32]: their bounds
     float* bD;         // [32]: re-check estimates at the start of the batch
     float* bE;         // [32]: their bounds
+    uint32_t* bPrior;  // [32]: 1 when a swap accepted in an earlier batch conflicts
+    uint32_t* bMask;   // [32]: earlier candidates of the same batch it conflicts with
 };
 
 __device__ __forceinline__ PairWalk pair_walk_arrays(uint32_t* base, int pair_cap, int M, int S) {
@@ -789,11 +863,13 @@ __device__ __forceinline__ PairWalk pair_walk_arrays(uint32_t* base, int pair_ca
     w.spec = p + (size_t)pair_cap * 8;
     p += align_up((uint32_t)pair_cap * 10, 16);
     w.dense = reinterpret_cast<int8_t*>(p);
-    p += align_up(32u * (uint32_t)(M * S * S), 16);
+    p += align_up(32u * (((uint32_t)(M * S * S) + 3u) & ~3u), 16);
     w.X = reinterpret_cast<float*>(p);
     w.Xe = w.X + 32 * 32;
     w.bD = w.Xe + 32 * 32;
     w.bE = w.bD + 32;
+    w.bPrior = reinterpret_cast<uint32_t*>(w.bE + 32);
+    w.bMask = w.bPrior + 32;
     return w;
 }
 
@@ -882,28 +958,48 @@ __device__ void walk_pairs(const ChainDesc& d, ChainSmem& m, ChainShared& sh, co
         w.pos[r * 6 + 5] = (int16_t)Z;
     }
     __syncthreads();
-    // 2. Conflict matrix rows: bit i of row r (i < r) when candidates i and r conflict.
+    // 2. Conflict matrix rows: bit i of row r (i < r) when candidates i and r conflict.  One warp
+    // per word: lane l tests candidate i = 32 wd + l against r (a first-coordinate test rejects
+    // most pairs), and the ballot is the word.
     const int r2max = c_shells[KIND].radius2[M - 1];
     const int PX = 2 * c.g.Lx, PY = 2 * c.g.Ly, PZ = 2 * c.g.Lz;
-    for (int t = tid; t < ne * nw; t += T) {
-        const int r = t / nw, wd = t % nw;
-        uint32_t bits = 0;
-        const int i_end = min(r, 32 * wd + 32);
-        for (int i = 32 * wd; i < i_end; ++i) {
-            bool hit = false;
+    {
+        // Task (wd, rc): lanes hold candidates i = 32 wd + lane in registers; the warp sweeps the 32
+        // later candidates r = 32 rc .. 32 rc + 31 (rc >= wd), whose positions are broadcast loads.
+        const int warp = tid >> 5, nwarps = T >> 5;
+        const int ntasks = nw * (nw + 1) / 2;
+        for (int t = warp; t < ntasks; t += nwarps) {
+            int wd = 0, rem = t;
+            while (rem >= nw - wd) {   // task t -> (wd, rc), rc from wd to nw - 1
+                rem -= nw - wd;
+                ++wd;
+            }
+            const int rc = wd + rem;
+            const int i = 32 * wd + lane;
+            int pi[6];
 #pragma unroll
-            for (int u = 0; u < 2; ++u)
+            for (int q = 0; q < 6; ++q) pi[q] = (i < ne) ? w.pos[i * 6 + q] : 0;
+            const int r_end = min(ne, 32 * rc + 32);
+            for (int r = 32 * rc; r < r_end; ++r) {
+                bool hit = false;
+                if (i < r) {
 #pragma unroll
-                for (int v = 0; v < 2; ++v) {
-                    const int dx = wrap_min_image(w.pos[r * 6 + 3 * v] - w.pos[i * 6 + 3 * u], PX);
-                    const int dy = wrap_min_image(w.pos[r * 6 + 3 * v + 1] - w.pos[i * 6 + 3 * u + 1], PY);
-                    const int dz = wrap_min_image(w.pos[r * 6 + 3 * v + 2] - w.pos[i * 6 + 3 * u + 2], PZ);
-                    hit |= (dx * dx + dy * dy + dz * dz) <= r2max;
+                    for (int u = 0; u < 2; ++u)
+#pragma unroll
+                        for (int v = 0; v < 2; ++v) {
+                            const int dx = wrap_min_image(w.pos[r * 6 + 3 * v] - pi[3 * u], PX);
+                            if (dx * dx > r2max) continue;
+                            const int dy = wrap_min_image(w.pos[r * 6 + 3 * v + 1] - pi[3 * u + 1], PY);
+                            const int dz = wrap_min_image(w.pos[r * 6 + 3 * v + 2] - pi[3 * u + 2], PZ);
+                            hit |= (dx * dx + dy * dy + dz * dz) <= r2max;
+                        }
                 }
-            bits |= hit ? (1u << (i - 32 * wd)) : 0u;
+                const uint32_t bits = __ballot_sync(0xFFFFFFFFu, hit);
+                if (lane == 0) w.conf[r * nw + wd] = bits;
+            }
         }
-        w.conf[r * nw + wd] = bits;
     }
+    for (int x = tid; x < nw; x += T) sh.taken[x] = 0u;
     __syncthreads();
     // 3. The walk, in batches of up to 32 ranked candidates.  For each batch, in parallel: the dense
     // count changes of its candidates, their re-check estimates against the running state at the
@@ -913,8 +1009,7 @@ __device__ void walk_pairs(const ChainDesc& d, ChainSmem& m, ChainShared& sh, co
     // scalar corrections, each decision on an interval whose bound covers the estimate, the cross
     // terms and their roundings (the exact binary64 key when it cannot decide).  The accepted swaps
     // are applied to counts, species and FP32 coefficients in parallel at the end of the batch.
-    const int E = c.E, warp = tid >> 5, nwarps = T >> 5;
-    uint32_t taken = 0;   // warp 0: lane l holds bits 32 l .. 32 l + 31 of the accepted set
+    const int E = c.E, Ep = (E + 3) & ~3, warp = tid >> 5, nwarps = T >> 5;
     if (tid == 0) {
         sh.n_acc = 0;
         sh.walk_done = 0;
@@ -925,105 +1020,173 @@ __device__ void walk_pairs(const ChainDesc& d, ChainSmem& m, ChainShared& sh, co
         const int nb = min(32, ne - r0);
         const int acc_before = sh.n_acc;
         // P1: dense count changes of the batch.
-        for (int x = tid; x < nb * E; x += T) w.dense[x] = 0;
+        for (int x = tid; x < nb * Ep / 4; x += T) reinterpret_cast<uint32_t*>(w.dense)[x] = 0u;
         __syncthreads();
         for (int x = tid; x < nb * MP; x += T) {
             const int j = x / MP, f = x - j * MP;
             if (f < w.nlist[r0 + j]) {
                 const uint32_t v = w.list[(r0 + j) * MP + f];
-                w.dense[j * E + (int)(v & 0xFFu)] = (int8_t)(v >> 8);
+                w.dense[j * Ep + (int)(v & 0xFFu)] = (int8_t)(v >> 8);
             }
         }
-        // P2: re-check estimates at the start of the batch.
-        {
-            for (int j = warp; j < nb; j += nwarps) {
-                const int r = r0 + j, cnt = w.nlist[r];
-                float acc = 0.f, err = 0.f;
-                for (int x = lane; x < cnt; x += 32) {
-                    const uint32_t v = w.list[r * MP + x];
-                    const int e = (int)(v & 0xFFu);
-                    const float xf = (float)(int)(int8_t)(v >> 8), ax = fabsf(xf);
-                    acc = fmaf(xf, fmaf(m.fa[e], xf, m.fb[e]), acc);
-                    err = fmaf(ax, fmaf(c.rel * fabsf(m.fa[e]), ax, fmaf(c.rel, fabsf(m.fb[e]), m.beta[e])), err);
-                }
+        // P2: re-check estimates at the start of the batch, and each candidate's conflicts with the
+        // swaps accepted in earlier batches and with the earlier candidates of this batch.
+        for (int j = warp; j < nb; j += nwarps) {
+            const int r = r0 + j, cnt = w.nlist[r];
+            float acc = 0.f, err = 0.f;
+            for (int x = lane; x < cnt; x += 32) {
+                const uint32_t v = w.list[r * MP + x];
+                const int e = (int)(v & 0xFFu);
+                const float xf = (float)(int)(int8_t)(v >> 8), ax = fabsf(xf);
+                acc = fmaf(xf, fmaf(m.fa[e], xf, m.fb[e]), acc);
+                err = fmaf(ax, fmaf(c.rel * fabsf(m.fa[e]), ax, fmaf(c.rel, fabsf(m.fb[e]), m.beta[e])), err);
+            }
+            const bool prior = (lane <= (r >> 5)) && ((w.conf[r * nw + lane] & sh.taken[lane]) != 0u);
+            const uint32_t any_prior = __ballot_sync(0xFFFFFFFFu, prior);
 #pragma unroll
-                for (int o = 16; o > 0; o >>= 1) {
-                    acc += __shfl_xor_sync(0xFFFFFFFFu, acc, o);
-                    err += __shfl_xor_sync(0xFFFFFFFFu, err, o);
-                }
-                if (lane == 0) {
-                    w.bD[j] = acc;
-                    w.bE[j] = fmaf(err, 1.0f + 64.0f * kTwoUlp, kAbsBound);
-                }
+            for (int o = 16; o > 0; o >>= 1) {
+                acc += __shfl_xor_sync(0xFFFFFFFFu, acc, o);
+                err += __shfl_xor_sync(0xFFFFFFFFu, err, o);
+            }
+            if (lane == 0) {
+                w.bD[j] = acc;
+                w.bE[j] = fmaf(err, 1.0f + 64.0f * kTwoUlp, kAbsBound);
+                w.bPrior[j] = any_prior != 0u ? 1u : 0u;
+                w.bMask[j] = w.conf[r * nw + (r0 >> 5)] & ((1u << j) - 1u);
             }
         }
         __syncthreads();
-        // P3: cross terms of the batch, X(i, j) for i < j, with bounds (n_i + 4) 2^-23 sum |a dN_i dN_j|.
+        // P3: cross terms of the batch, X(i, j) = sum_e a_e dN_i dN_j for i < j, from the dense rows
+        // four entries at a time, with bounds (E + 4) 2^-23 sum |a dN_i dN_j|.
         for (int x = tid; x < 32 * 32; x += T) {
             const int i = x >> 5, j = x & 31;
             if (i >= j || j >= nb) continue;
-            const int r = r0 + i, cnt = w.nlist[r];
+            const uint32_t* di = reinterpret_cast<const uint32_t*>(w.dense + i * Ep);
+            const uint32_t* dj = reinterpret_cast<const uint32_t*>(w.dense + j * Ep);
             float X = 0.f, mag = 0.f;
-            for (int y = 0; y < cnt; ++y) {
-                const uint32_t v = w.list[r * MP + y];
-                const int e = (int)(v & 0xFFu);
-                const int dj = w.dense[j * E + e];
-                if (dj == 0) continue;
-                const float p = (float)((int)(int8_t)(v >> 8) * dj);
-                X = fmaf(m.fa[e], p, X);
-                mag = fmaf(fabsf(m.fa[e]), fabsf(p), mag);
+            for (int q4 = 0; q4 < Ep / 4; ++q4) {
+                const uint32_t u = di[q4], v = dj[q4];
+                if (u == 0u || v == 0u) continue;
+#pragma unroll
+                for (int b = 0; b < 4; ++b) {
+                    const int p = (int)(int8_t)(u >> (8 * b)) * (int)(int8_t)(v >> (8 * b));
+                    if (p == 0) continue;
+                    const float fa = m.fa[4 * q4 + b], pf = (float)p;
+                    X = fmaf(fa, pf, X);
+                    mag = fmaf(fabsf(fa), fabsf(pf), mag);
+                }
             }
             w.X[i * 32 + j] = X;
-            w.Xe[i * 32 + j] = fmaf(mag, (float)(cnt + 4) * kTwoUlp, kAbsBound);
+            w.Xe[i * 32 + j] = fmaf(mag, c.rel, kAbsBound);
         }
         __syncthreads();
-        // P4: decisions, in order, by warp 0.
+        // P4: decisions, in order, by warp 0; lane j holds candidate j's estimate, bound and conflict
+        // information.  Speculation: every undecided lane evaluates its candidate assuming that all
+        // earlier undecided candidates not blocked by earlier batches are accepted; the first lane
+        // whose decision contradicts that assumption ends the round: the lanes before it are
+        // committed (their assumptions held), it is decided under the committed state, and the next
+        // round starts after it.  Rounds = rejections + 1.
         if (warp == 0) {
-            float corr = 0.f, corrE = 0.f;   // lane j: sum of X(i, j) over accepted i of this batch, and bound
-            int n_acc = acc_before, nbacc = 0;
-            for (int j = 0; j < nb; ++j) {
+            float D0 = 0.f, E0 = 0.f;
+            uint32_t prior = 1u, mask = 0u;
+            if (lane < nb) {
+                D0 = w.bD[lane];
+                E0 = w.bE[lane];
+                prior = w.bPrior[lane];
+                mask = w.bMask[lane];
+            }
+            const uint32_t open = __ballot_sync(0xFFFFFFFFu, lane < nb && prior == 0u);
+            float cc = 0.f, ce = 0.f, ca = 0.f;   // corrections from committed accepted candidates
+            uint32_t accm = 0u;                  // committed accepted candidates of the batch
+            int n_acc = acc_before, nbacc = 0, p = 0;
+            bool done = false;
+            while (p < nb && !done) {
+                const uint32_t below_p = (p >= 32) ? 0xFFFFFFFFu : ((1u << p) - 1u);
+                const uint32_t guess = open & ~below_p;
+                int dec = 0;
+                if (lane >= p && lane < nb) {
+                    const uint32_t gl = guess & ((1u << lane) - 1u);
+                    float s = cc, e = ce, a = ca;
+                    for (uint32_t bits = gl; bits; bits &= bits - 1u) {
+                        const int i = __ffs(bits) - 1;
+                        const float x = w.X[i * 32 + lane];
+                        s += x;
+                        e += w.Xe[i * 32 + lane];
+                        a += fabsf(x);
+                    }
+                    const bool blocked = prior != 0u || (mask & (accm | gl)) != 0u;
+                    if (!blocked) {
+                        if (acc_before == 0 && (accm | gl) == 0u) {
+                            dec = 1;   // the step-start state: the candidate is eligible
+                        } else {
+                            const float v = fmaf(2.0f, s, D0);
+                            const float er = fmaf(fmaf(2.0f, e, E0), 1.0f + 2.0f * 64.0f * kTwoUlp,
+                                                  fmaf(40.0f * kTwoUlp, fabsf(D0) + 2.0f * a, kAbsBound));
+                            dec = eligible_interval(__fadd_rd(v, -er), __fadd_ru(v, er), c.pos_thr, c.thr_lo,
+                                                    c.thr_hi);
+                        }
+                    }
+                }
+                const uint32_t bad =
+                    __ballot_sync(0xFFFFFFFFu, lane >= p && lane < nb && prior == 0u && dec != 1);
+                const int js = bad ? (__ffs(bad) - 1) : nb;
+                // Commit the accepted candidates of [p, js), at most max_accept in total.
+                uint32_t commit = guess & ((js >= 32) ? 0xFFFFFFFFu : ((1u << js) - 1u));
+                if (d.max_accept > 0) {
+                    const int room = d.max_accept - n_acc;
+                    while (__popc(commit) > room) commit &= ~(1u << (31 - __clz(commit)));
+                    if (__popc(guess & ((js >= 32) ? 0xFFFFFFFFu : ((1u << js) - 1u))) > room) done = true;
+                }
+                for (uint32_t bits = commit; bits; bits &= bits - 1u) {
+                    const int i = __ffs(bits) - 1;
+                    if (lane == 0) sh.red_q[nbacc] = i;
+                    if (lane > i && lane < nb) {
+                        const float x = w.X[i * 32 + lane];
+                        cc += x;
+                        ce += w.Xe[i * 32 + lane];
+                        ca += fabsf(x);
+                    }
+                    ++nbacc;
+                }
+                accm |= commit;
+                n_acc += __popc(commit);
+                if (done || js >= nb) break;
                 if (d.max_accept > 0 && n_acc >= d.max_accept) {
-                    if (lane == 0) sh.walk_done = 1;
+                    done = true;
                     break;
                 }
-                const int r = r0 + j;
-                const bool hit = (lane < nw) && ((w.conf[r * nw + lane] & taken) != 0u);
-                if (__any_sync(0xFFFFFFFFu, hit)) continue;
-                int verdict = 1;   // before the first accept of the step the state is the step-start state
-                if (n_acc > 0) {
-                    if (lane == j) {
-                        const float D0 = w.bD[j], E0 = w.bE[j];
-                        const float v = fmaf(2.0f, corr, D0);
-                        const float er = fmaf(fmaf(2.0f, corrE, E0), 1.0f + 2.0f * 64.0f * kTwoUlp,
-                                              fmaf(2.0f * kTwoUlp, fabsf(D0) + 2.0f * fabsf(corr), kAbsBound));
-                        verdict = eligible_interval(__fadd_rd(v, -er), __fadd_ru(v, er), c.pos_thr, c.thr_lo, c.thr_hi);
+                // Decide candidate js under the committed state.
+                int dj = __shfl_sync(0xFFFFFFFFu, dec, js);
+                if (dj < 0) {
+                    const int r = r0 + js;
+                    double Dp = 0.0;
+                    if (lane == 0) {
+                        const uint32_t q = m.order[r];
+                        Dp = exact_key_pending(M, S, m.cnt, m.Q, m.tgt, m.ca, d.w, w.spec[2 * r], w.spec[2 * r + 1],
+                                               m.qg + q * M, w.dense, Ep, sh.red_q, nbacc);
                     }
-                    verdict = __shfl_sync(0xFFFFFFFFu, verdict, j);
-                    if (verdict < 0) {
-                        double Dp = 0.0;
-                        if (lane == 0) {
-                            const uint32_t q = m.order[r];
-                            Dp = exact_key_pending(M, S, m.cnt, m.Q, m.tgt, m.ca, d.w, w.spec[2 * r],
-                                                   w.spec[2 * r + 1], m.qg + q * M, w.dense, E, sh.red_q, nbacc);
-                        }
-                        Dp = __shfl_sync(0xFFFFFFFFu, Dp, 0);
-                        verdict = eligible(Dp, false, c.thr) ? 1 : 0;
+                    Dp = __shfl_sync(0xFFFFFFFFu, Dp, 0);
+                    dj = eligible(Dp, false, c.thr) ? 1 : 0;
+                }
+                if (dj == 1) {
+                    if (lane == 0) sh.red_q[nbacc] = js;
+                    if (lane > js && lane < nb) {
+                        const float x = w.X[js * 32 + lane];
+                        cc += x;
+                        ce += w.Xe[js * 32 + lane];
+                        ca += fabsf(x);
                     }
+                    ++nbacc;
+                    ++n_acc;
+                    accm |= 1u << js;
+                    if (d.max_accept > 0 && n_acc >= d.max_accept) done = true;
                 }
-                if (verdict != 1) continue;
-                if (lane == (r >> 5)) taken |= 1u << (r & 31);
-                if (lane == 0) sh.red_q[nbacc] = j;
-                if (lane > j && lane < nb) {
-                    corr += w.X[j * 32 + lane];
-                    corrE += w.Xe[j * 32 + lane] + kTwoUlp * fabsf(corr);
-                }
-                ++nbacc;
-                ++n_acc;
-                __syncwarp();
+                p = js + 1;
             }
             if (lane == 0) {
                 sh.batch_n = nbacc;
                 sh.n_acc = n_acc;
+                if (done) sh.walk_done = 1;
             }
         }
         __syncthreads();
@@ -1042,6 +1205,7 @@ __device__ void walk_pairs(const ChainDesc& d, ChainSmem& m, ChainShared& sh, co
             store_species_atomic<BITS>(m.types, w.site[2 * r], w.spec[2 * r + 1]);
             store_species_atomic<BITS>(m.types, w.site[2 * r + 1], w.spec[2 * r]);
             m.acc[acc_before + x] = m.order[r];
+            atomicOr(&sh.taken[r >> 5], 1u << (r & 31));
         }
         __syncthreads();
         // P6: running FP32 coefficients of every entry (an entry whose change returned to 0 needs
