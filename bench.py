@@ -146,13 +146,14 @@ def run_ours(args):
     obj = hea.Objective(spec.n_per, spec.weights(), spec.targets())
     N, S, M = lat.N, spec.S, spec.M
     ctas = torch.cuda.get_device_properties(local).multi_processor_count
-    K = ctas * COOP_KC
+    coop_kc, coop_top = args.coop_kc, args.coop_top
+    K = ctas * coop_kc
     steps_per_call = max(1, args.trials // K)
     trials_per_step = steps_per_call * K
     workspace = torch.zeros(hea.hea_search_coop_workspace_bytes(ctas), dtype=torch.uint8, device="cuda")
 
     def search(step_seed):
-        params = hea.search_params(K, steps_per_call, accept_mode=1, group_size=COOP_KC, group_top=COOP_TOP,
+        params = hea.search_params(K, steps_per_call, accept_mode=1, group_size=coop_kc, group_top=coop_top,
                                    seed=step_seed)
         hea.hea_search_coop(lat, obj, params, ctas, types, counts, result, workspace, stream)
 
@@ -258,8 +259,10 @@ def run_ours(args):
         "metric": METRIC, "value": value, "unit": "trials/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "u8+i32+f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD if args.trials == TRIALS_PER_STEP else
-                   WORKLOAD.replace("1e8 swap trials", f"{trials_per_step} swap trials"),
+        "config": {"workload": (WORKLOAD if args.trials == TRIALS_PER_STEP else
+                                WORKLOAD.replace("1e8 swap trials", f"{trials_per_step} swap trials")).replace(
+                                    "512 candidates per CTA", f"{coop_kc} candidates per CTA").replace(
+                                    "best 2 per CTA", f"best {coop_top} per CTA"),
                    "sites": N, "trials_per_step": trials_per_step, "K": K, "ctas": ctas, "search_steps": steps_per_call,
                    "accept_mode": "multi", "l2": "flushed between timed steps (256 MiB write)",
                    "parallelism": f"replicas x{world}"},
@@ -276,7 +279,7 @@ def run_ours(args):
         line["recount"] = run_recount(torch, hea)
         line["serve"] = run_serving(args.serve_requests)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(args.cpu_steps, ctas)
+        line["cpu_baseline"] = cpu_baseline(args.cpu_steps, ctas, coop_kc, coop_top)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -402,20 +405,20 @@ def oracle_free_initial(spec, N):
 # ------------------------------------------------------------------------------------------------
 # CPU oracle (baseline leg and reference arm)
 # ------------------------------------------------------------------------------------------------
-def cpu_baseline(n_steps, ctas=SM_COUNT):
+def cpu_baseline(n_steps, ctas=SM_COUNT, coop_kc=COOP_KC, coop_top=COOP_TOP):
     """The plain serial oracle on a bounded sample of the same workload: init, recount, then n_steps
     search steps with the benchmark's candidate set and accept rule (K = ctas x 512 candidates per
     step, the best 2 eligible of every 512 walked).  Returns trials/s of the search part."""
     import oracle
     spec = workload_inputs()
     N = spec.N
-    K = ctas * COOP_KC
+    K = ctas * coop_kc
     t0 = time.perf_counter()
     types = oracle.init_config(N, spec.n_per, spec.seed)
     cnt = oracle.counts(spec.kind, spec.L, spec.M, spec.S, types)
     t1 = time.perf_counter()
     _, _, res, _ = oracle.search(spec.kind, spec.L, spec.M, spec.n_per, spec.weights(), spec.targets(), types, cnt,
-                                 K=K, max_steps=n_steps, accept_mode=1, group_size=COOP_KC, group_top=COOP_TOP,
+                                 K=K, max_steps=n_steps, accept_mode=1, group_size=coop_kc, group_top=coop_top,
                                  seed=spec.seed)
     t2 = time.perf_counter()
     trials = res["trials"]
@@ -462,6 +465,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-secondary", action="store_true", help="skip the batched, recount and serving measurements")
     ap.add_argument("--serve-requests", type=int, default=300)
+    ap.add_argument("--coop-kc", type=int, default=COOP_KC, help="candidates per CTA per search step")
+    ap.add_argument("--coop-top", type=int, default=COOP_TOP, help="best eligible candidates per CTA walked")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)

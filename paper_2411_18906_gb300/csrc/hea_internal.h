@@ -47,6 +47,17 @@ struct ChainLayout {
 
 __host__ __device__ inline uint32_t align_up(uint32_t x, uint32_t a) { return (x + a - 1) / a * a; }
 
+// The site grid that finds conflicting candidates: at most 2048 bins (list heads), then per site
+// its next pointer and its packed bin coordinates.
+constexpr uint32_t kConflictBins = 2048;
+
+// Scratch shared by the conflict grid (before the walk's batches) and the batch data.
+__host__ __device__ inline uint32_t scratch_bytes(int n, uint32_t E) {
+    const uint32_t batch = align_up(32 * ((E + 3) & ~3u), 16) + 2 * 32 * 32 * 4 + 4 * 32 * 4;
+    const uint32_t hash = 4 * kConflictBins + 8 * 2 * (uint32_t)n;   // heads, next pointers, site bins
+    return batch > hash ? batch : hash;
+}
+
 // Bytes of the pairwise-walk data for a ranked list of up to n candidates: per candidate its
 // nonzero count changes (2 bytes each, M (4S - 4) at most), its count, its two sites' coordinates
 // (6 int16), its row of the conflict matrix (ceil(n / 32) words) and its sites and species; then
@@ -60,7 +71,7 @@ __host__ __device__ inline uint32_t pair_walk_bytes(int n, int M, int S) {
            // batch scratch of the walk: dense count changes (int8 [32][E rounded up to 4]), cross
            // terms and their bounds (float [32][32] each), estimates, their bounds and the conflict
            // information of the batch's candidates ([32] each)
-           align_up(32 * ((E + 3) & ~3u), 16) + 2 * 32 * 32 * 4 + 4 * 32 * 4;
+           scratch_bytes(n, E);
 }
 
 // qcap: candidate slots (the candidates a CTA scores per step, or the merged records of a

@@ -642,7 +642,7 @@ __device__ int block_compact(const uint32_t* src, int n, uint32_t* dst, Keep kee
 // best of each group (k / group_size) stay.  Sets sh.n_elig.
 template <int BITS>
 __device__ void rank_eligible(ChainSmem& m, ChainShared& sh, const ChainCtx& c, int n, int group_size,
-                              int group_top) {
+                              int group_top, bool single_group) {
     const int tid = threadIdx.x, T = blockDim.x;
     if (tid == 0) sh.n_elig = 0;
     __syncthreads();
@@ -674,7 +674,7 @@ __device__ void rank_eligible(ChainSmem& m, ChainShared& sh, const ChainCtx& c, 
     });
     float* pm = reinterpret_cast<float*>(m.qkey);   // prefix maxima of the upper bounds (ping-pong)
     float* pm2 = pm + c.qcap;
-    for (int s = tid; s < ne; s += T) pm[s] = m.qhi[m.order[s] & 0x7FFFFFFFu];
+    for (int s = tid; s < ne; s += T) pm[s] = m.qhi[m.order[s] & 0x3FFFFFFFu];
     __syncthreads();
     for (int dd = 1; dd < ne; dd <<= 1) {
         for (int s = tid; s < ne; s += T) pm2[s] = (s >= dd) ? fmaxf(pm[s], pm[s - dd]) : pm[s];
@@ -683,12 +683,20 @@ __device__ void rank_eligible(ChainSmem& m, ChainShared& sh, const ChainCtx& c, 
         pm = pm2;
         pm2 = tmp;
     }
+    // Cluster starts (bit 30): no earlier interval reaches this one.  Clusters are contiguous in
+    // this order and strictly ordered against each other.
     for (int s = tid; s < ne; s += T) {
-        const uint32_t x = m.order[s];
+        const uint32_t q = m.order[s] & 0x3FFFFFFFu;
+        const bool start = (s == 0) || (pm[s - 1] < m.qlo[q]);
+        if (start) m.order[s] |= 0x40000000u;
+    }
+    __syncthreads();
+    for (int s = tid; s < ne; s += T) {
+        const uint32_t x = m.order[s] & ~0x40000000u;
         if (x & 0x80000000u) continue;   // already exact
         const uint32_t q = x & 0x7FFFFFFFu;
         const bool before = (s > 0) && (pm[s - 1] >= m.qlo[q]);
-        const bool after = (s + 1 < ne) && (m.qlo[m.order[s + 1] & 0x7FFFFFFFu] <= m.qhi[q]);
+        const bool after = (s + 1 < ne) && (m.qlo[m.order[s + 1] & 0x3FFFFFFFu] <= m.qhi[q]);
         if (before || after) {
             const int A = load_species<BITS>(m.types, m.qa[q]), B = load_species<BITS>(m.types, m.qb[q]);
             m.qD[q] = exact_key(c.M, c.S, m.ca, m.cb, A, B, m.qg + q * c.M);
@@ -701,23 +709,50 @@ __device__ void rank_eligible(ChainSmem& m, ChainShared& sh, const ChainCtx& c, 
         m.qkey[q] = order_key(m.qD[q]);
     }
     __syncthreads();
-    // Ranking by (group, key, k); the group rule keeps the first group_top of every group.
-    const uint32_t G = (group_top > 0) ? (uint32_t)(group_size > 0 ? group_size : c.K) : 0xFFFFFFFFu;
-    block_sort(m.acc, ne, [&](uint32_t x, uint32_t y) {
-        const uint32_t gx = m.qk[x] / G, gy = m.qk[y] / G;
-        return gx < gy || (gx == gy && better_key(m.qkey[x], m.qk[x], m.qkey[y], m.qk[y]));
-    });
     int keep = ne;
-    if (group_top > 0) {
+    if (single_group) {
+        // The order by lower bound, with every cluster sorted by (key, k), is the order by (D, k).
+        if (tid == 0) sh.red_k[0] = 0u;
+        __syncthreads();
+        for (int s = tid; s < ne; s += T) {
+            if ((m.order[s] & 0x40000000u) == 0u) continue;
+            int e = s + 1;
+            while (e < ne && (m.order[e] & 0x40000000u) == 0u) ++e;
+            if (e - s > 1) atomicMax(&sh.red_k[0], (uint32_t)(e - s));
+            if (e - s > 1 && e - s <= 32) {
+                for (int x = s; x < e; ++x) m.order[x] &= 0x3FFFFFFFu;
+                for (int x = s + 1; x < e; ++x) {
+                    const uint32_t v = m.order[x];
+                    int y = x - 1;
+                    while (y >= s && better_key(m.qkey[v], m.qk[v], m.qkey[m.order[y]], m.qk[m.order[y]])) {
+                        m.order[y + 1] = m.order[y];
+                        --y;
+                    }
+                    m.order[y + 1] = v;
+                }
+            }
+        }
+        __syncthreads();
+        for (int s = tid; s < ne; s += T) m.order[s] &= 0x3FFFFFFFu;
+        __syncthreads();
+        if (sh.red_k[0] > 32u)
+            block_sort(m.order, ne, [&](uint32_t x, uint32_t y) {
+                return better_key(m.qkey[x], m.qk[x], m.qkey[y], m.qk[y]);
+            });
+        if (group_top > 0 && keep > group_top) keep = group_top;
+    } else {
+        // Ranking by (group, key, k); the group rule keeps the first group_top of every group.
+        const uint32_t G = (uint32_t)(group_size > 0 ? group_size : c.K);
+        block_sort(m.acc, ne, [&](uint32_t x, uint32_t y) {
+            const uint32_t gx = m.qk[x] / G, gy = m.qk[y] / G;
+            return gx < gy || (gx == gy && better_key(m.qkey[x], m.qk[x], m.qkey[y], m.qk[y]));
+        });
         keep = block_compact(m.acc, ne, m.order, [&](int s) {
             return s < group_top || (m.qk[m.acc[s - group_top]] / G != m.qk[m.acc[s]] / G);
         }, sh);
         block_sort(m.order, keep, [&](uint32_t x, uint32_t y) {
             return better_key(m.qkey[x], m.qk[x], m.qkey[y], m.qk[y]);
         });
-    } else {
-        for (int s = tid; s < ne; s += T) m.order[s] = m.acc[s];
-        __syncthreads();
     }
     if (tid == 0) sh.n_elig = keep;
     __syncthreads();
@@ -958,44 +993,58 @@ __device__ void walk_pairs(const ChainDesc& d, ChainSmem& m, ChainShared& sh, co
         w.pos[r * 6 + 5] = (int16_t)Z;
     }
     __syncthreads();
-    // 2. Conflict matrix rows: bit i of row r (i < r) when candidates i and r conflict.  One warp
-    // per word: lane l tests candidate i = 32 wd + l against r (a first-coordinate test rejects
-    // most pairs), and the ballot is the word.
+    // 2. Conflict matrix rows: bit i of row r (i < r) when candidates i and r conflict.  The 2 ne
+    // sites are put in a grid of at most 2048 bins, each at least 4 half units wide (more than any
+    // shell radius), kept as linked lists; a site can only conflict with sites of its own and the 26
+    // neighbouring bins, which are tested by minimum-image distance.
     const int r2max = c_shells[KIND].radius2[M - 1];
     const int PX = 2 * c.g.Lx, PY = 2 * c.g.Ly, PZ = 2 * c.g.Lz;
     {
-        // Task (wd, rc): lanes hold candidates i = 32 wd + lane in registers; the warp sweeps the 32
-        // later candidates r = 32 rc .. 32 rc + 31 (rc >= wd), whose positions are broadcast loads.
-        const int warp = tid >> 5, nwarps = T >> 5;
-        const int ntasks = nw * (nw + 1) / 2;
-        for (int t = warp; t < ntasks; t += nwarps) {
-            int wd = 0, rem = t;
-            while (rem >= nw - wd) {   // task t -> (wd, rc), rc from wd to nw - 1
-                rem -= nw - wd;
-                ++wd;
-            }
-            const int rc = wd + rem;
-            const int i = 32 * wd + lane;
-            int pi[6];
+        uint32_t* head = reinterpret_cast<uint32_t*>(w.dense);   // the batch scratch, unused until the batches
+        uint32_t* next = head + kConflictBins;
+        uint32_t* sbin = next + 2 * ne;
+        int nbx = max(1, PX / 4), nby = max(1, PY / 4), nbz = max(1, PZ / 4);
+        while (nbx * nby * nbz > (int)kConflictBins) {
+            if (nbx >= nby && nbx >= nbz) nbx = (nbx + 1) / 2;
+            else if (nby >= nbz) nby = (nby + 1) / 2;
+            else nbz = (nbz + 1) / 2;
+        }
+        for (int x = tid; x < nbx * nby * nbz; x += T) head[x] = 0u;
+        for (int x = tid; x < ne * nw; x += T) w.conf[x] = 0u;
+        __syncthreads();
+        for (int s2 = tid; s2 < 2 * ne; s2 += T) {
+            const int16_t* P3 = w.pos + (s2 >> 1) * 6 + 3 * (s2 & 1);
+            const int bx = P3[0] * nbx / PX, by = P3[1] * nby / PY, bz = P3[2] * nbz / PZ;
+            sbin[s2] = (uint32_t)bx | ((uint32_t)by << 11) | ((uint32_t)bz << 22);
+            next[s2] = atomicExch(&head[(bz * nby + by) * nbx + bx], (uint32_t)s2 + 1u);
+        }
+        __syncthreads();
+        // One task per (site, layer of 9 neighbouring bins).
+        for (int t = tid; t < 2 * ne * 3; t += T) {
+            const int s2 = t / 3, lz = t - 3 * s2;
+            const int r = s2 >> 1;
+            const int16_t* P3 = w.pos + r * 6 + 3 * (s2 & 1);
+            const int X = P3[0], Y = P3[1], Z = P3[2];
+            const uint32_t bb = sbin[s2];
+            int cz = (int)(bb >> 22) + lz - 1;
+            cz += (cz < 0) ? nbz : 0;
+            cz -= (cz >= nbz) ? nbz : 0;
 #pragma unroll
-            for (int q = 0; q < 6; ++q) pi[q] = (i < ne) ? w.pos[i * 6 + q] : 0;
-            const int r_end = min(ne, 32 * rc + 32);
-            for (int r = 32 * rc; r < r_end; ++r) {
-                bool hit = false;
-                if (i < r) {
-#pragma unroll
-                    for (int u = 0; u < 2; ++u)
-#pragma unroll
-                        for (int v = 0; v < 2; ++v) {
-                            const int dx = wrap_min_image(w.pos[r * 6 + 3 * v] - pi[3 * u], PX);
-                            if (dx * dx > r2max) continue;
-                            const int dy = wrap_min_image(w.pos[r * 6 + 3 * v + 1] - pi[3 * u + 1], PY);
-                            const int dz = wrap_min_image(w.pos[r * 6 + 3 * v + 2] - pi[3 * u + 2], PZ);
-                            hit |= (dx * dx + dy * dy + dz * dz) <= r2max;
-                        }
+            for (int q9 = 0; q9 < 9; ++q9) {
+                int cx = (int)(bb & 2047u) + (q9 % 3) - 1, cy = (int)((bb >> 11) & 2047u) + q9 / 3 - 1;
+                cx += (cx < 0) ? nbx : 0;
+                cx -= (cx >= nbx) ? nbx : 0;
+                cy += (cy < 0) ? nby : 0;
+                cy -= (cy >= nby) ? nby : 0;
+                for (uint32_t x = head[(cz * nby + cy) * nbx + cx]; x != 0u; x = next[x - 1]) {
+                    const int t2 = (int)x - 1, i = t2 >> 1;
+                    if (i >= r) continue;
+                    const int16_t* Q3 = w.pos + i * 6 + 3 * (t2 & 1);
+                    const int dx = wrap_min_image(X - Q3[0], PX);
+                    const int dy = wrap_min_image(Y - Q3[1], PY);
+                    const int dz = wrap_min_image(Z - Q3[2], PZ);
+                    if (dx * dx + dy * dy + dz * dz <= r2max) atomicOr(&w.conf[r * nw + (i >> 5)], 1u << (i & 31));
                 }
-                const uint32_t bits = __ballot_sync(0xFFFFFFFFu, hit);
-                if (lane == 0) w.conf[r * nw + wd] = bits;
             }
         }
     }
@@ -1336,7 +1385,8 @@ __device__ void run_chain(const ChainDesc& d, uint8_t* smem, ChainShared& sh) {
             }
         } else {
             __syncthreads();
-            rank_eligible<BITS>(m, sh, c, sh.qn, d.group_size, d.group_top);
+            rank_eligible<BITS>(m, sh, c, sh.qn, d.group_size, d.group_top,
+                                d.group_top == 0 || d.group_size == 0 || d.group_size >= c.K);
             walk<KIND, BITS>(d, m, sh, c, sh.n_elig);
             after_walk<KIND>(d, m, sh, c);
         }
@@ -1421,7 +1471,7 @@ __device__ void run_coop_chain(const ChainDesc& d, uint8_t* smem, ChainShared& s
             }
         } else {
             __syncthreads();
-            rank_eligible<BITS>(m, sh, c, sh.qn, (int)Kc, top);
+            rank_eligible<BITS>(m, sh, c, sh.qn, (int)Kc, top, true);
             n_pub = min(sh.n_elig, top);
         }
         // Publish this CTA's candidates for the step (double-buffered by step parity).
@@ -1482,7 +1532,7 @@ __device__ void run_coop_chain(const ChainDesc& d, uint8_t* smem, ChainShared& s
         } else {
             // The published candidates are eligible; ranking them across CTAs computes exact keys
             // where intervals from different CTAs overlap.
-            rank_eligible<BITS>(m, sh, c, sh.qn, 0, 0);
+            rank_eligible<BITS>(m, sh, c, sh.qn, 0, 0, true);
             walk<KIND, BITS>(d, m, sh, c, sh.n_elig);
             after_walk<KIND>(d, m, sh, c);
         }

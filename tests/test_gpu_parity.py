@@ -343,3 +343,19 @@ def test_search_multi_accept_group_rule_bit_exact(kind, L, M, S, K, G, top, step
     g, o = run_both(kind, L, M, S, n_per, w, target, 3, K=K, max_steps=steps, accept_mode=1, group_size=G,
                     group_top=top, seed=11)
     assert_same(g, o)
+
+
+@pytest.mark.parametrize("mode,K", [(0, 512), (1, 512), (1, 2048)])
+def test_search_massive_key_ties_from_ordered_start(mode, K):
+    """B2-ordered BCC 8^3 with a zero target: swaps with identical surroundings have bit-identical
+    keys, so hundreds of candidates tie and are ordered by k alone (large overlap clusters)."""
+    kind, L, M, S = BCC, (8, 8, 8), 3, 2
+    pos = oracle.positions(kind, L)
+    t = (pos[:, 0] % 2).astype(np.uint8)
+    n_per = [512, 512]
+    cnt = oracle.counts(kind, L, M, S, t)
+    w, target = np.ones(M), np.zeros((M, S, S))
+    tg, cg, rg = G.gpu_search(kind, L, M, n_per, w, target, t, cnt, K=K, max_steps=6, accept_mode=mode, seed=3)
+    to, co, ro, _ = oracle.search(kind, L, M, n_per, w, target, t, cnt, K=K, max_steps=6, accept_mode=mode, seed=3)
+    assert_same((tg, cg, rg), (to, co, ro))
+    assert ro["accepted"] > 0
