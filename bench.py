@@ -28,11 +28,11 @@ from paper_2411_18906_gb300 import workloads  # noqa: E402
 METRIC = "Δ-SRO swap trials/s at 256k-atom FCC; batched cells/s; p99 serve latency"
 SEARCH_K = 256           # candidates per step of the single-CTA chain (parity tests, CPU sample)
 COOP_KC = 512            # candidates per CTA per step of the cooperative chain
-COOP_TOP = 2             # best eligible candidates per CTA that enter the multi-accept walk
+COOP_TOP = 1             # best eligible candidates per CTA that enter the multi-accept walk
 TRIALS_PER_STEP = 100_000_000
 WORKLOAD = "FCC 40x40x40 (256,000 sites), 4 species 40/20/20/20, shells 1-3, annealed target, " \
            "1e8 swap trials per step, multi-accept, one chain over all SMs (512 candidates per CTA per " \
-           "search step, best 2 per CTA walked)"
+           "search step, best 1 per CTA walked)"
 SM_COUNT = 152
 SM_MAX_MHZ = 2070.0
 
@@ -262,7 +262,7 @@ def run_ours(args):
         "config": {"workload": (WORKLOAD if args.trials == TRIALS_PER_STEP else
                                 WORKLOAD.replace("1e8 swap trials", f"{trials_per_step} swap trials")).replace(
                                     "512 candidates per CTA", f"{coop_kc} candidates per CTA").replace(
-                                    "best 2 per CTA", f"best {coop_top} per CTA"),
+                                    "best 1 per CTA", f"best {coop_top} per CTA"),
                    "sites": N, "trials_per_step": trials_per_step, "K": K, "ctas": ctas, "search_steps": steps_per_call,
                    "accept_mode": "multi", "l2": "flushed between timed steps (256 MiB write)",
                    "parallelism": f"replicas x{world}"},

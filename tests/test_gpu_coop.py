@@ -85,13 +85,17 @@ def test_coop_time_budget():
     assert np.array_equal(cg, oracle.counts(kind, L, M, S, tg))
 
 
-def test_coop_fcc_256k_all_sms_prefix():
-    """FCC 40^3 with the annealed target on every SM, multi-accept with group_top 2: a prefix of the
-    trajectory bit-exact against the oracle."""
+@pytest.mark.parametrize("top", [1, 2])
+def test_coop_fcc_256k_all_sms_prefix(top):
+    """FCC 40^3 with the annealed target on every SM in the benchmark's launch configuration
+    (candidates per CTA and published candidates per CTA from bench.py, and one other): a prefix of
+    the trajectory bit-exact against the oracle."""
+    from bench import COOP_KC, COOP_TOP
     spec = workloads.fcc_256k()
     ctas = G.sm_count()
-    Kc = 512
-    kw = dict(K=ctas * Kc, max_steps=6, accept_mode=1, group_size=Kc, group_top=2, seed=1)
+    Kc = COOP_KC
+    kw = dict(K=ctas * Kc, max_steps=6, accept_mode=1, group_size=Kc, group_top=(COOP_TOP if top == 1 else top),
+              seed=1)
     g, o, _, _ = both(spec.kind, spec.L, spec.M, spec.S, spec.n_per, spec.weights(), spec.targets(), spec.seed,
                       ctas, **kw)
     assert_same(g, o)
