@@ -47,8 +47,8 @@ __global__ void __launch_bounds__(256) delta_swap_kernel(const __grid_constant__
         return;
     }
     uint64_t ha[M], hb[M];
-    neighbour_histogram<KIND, M>(g, a, b, onehot, ha);
-    neighbour_histogram<KIND, M>(g, b, a, onehot, hb);
+    neighbour_histogram_upto<KIND, M>(g, a, b, onehot, ha, M);
+    neighbour_histogram_upto<KIND, M>(g, b, a, onehot, hb, M);
     uint64_t gb[M];
 #pragma unroll
     for (int k = 0; k < M; ++k) gb[k] = pack_g(ha[k], hb[k]);

@@ -236,54 +236,68 @@ struct ShellsOf {
 };
 
 // One-hot species increment of the neighbour reached by shell vector V (a compile-time index, so
-// the offsets are immediates and the axis table stays in registers).
-template <int KIND, int R, int V, typename OneHot>
-__device__ __forceinline__ uint64_t vector_increment(const AxisTable<KIND, R>& ax, uint32_t excl, OneHot& onehot) {
+// the offsets are immediates and the axis table stays in registers).  H is the accumulator type
+// (32 bits hold four 8-bit species fields, 64 bits eight); with EXCL the neighbour `excl` is skipped.
+template <int KIND, int R, int V, bool EXCL, typename H, typename OneHot>
+__device__ __forceinline__ H vector_increment(const AxisTable<KIND, R>& ax, uint32_t excl, OneHot& onehot) {
     constexpr int dx = ShellsOf<KIND>::table.v[V][0] + R;
     constexpr int dy = ShellsOf<KIND>::table.v[V][1] + R;
     constexpr int dz = ShellsOf<KIND>::table.v[V][2] + R;
     const uint32_t n = (uint32_t)(ax.x[dx] + ax.y[dy] + ax.z[dz]);
-    const uint64_t inc = onehot(n);
-    return (n != excl) ? inc : 0ull;
+    const H inc = onehot(n);
+    if (EXCL) return (n != excl) ? inc : (H)0;
+    return inc;
 }
 
-template <int KIND, int R, int FIRST, typename OneHot, int... I>
-__device__ __forceinline__ uint64_t shell_sum(const AxisTable<KIND, R>& ax, uint32_t excl, OneHot& onehot,
-                                              std::integer_sequence<int, I...>) {
-    return (0ull + ... + vector_increment<KIND, R, FIRST + I>(ax, excl, onehot));
+template <int KIND, int R, int FIRST, bool EXCL, typename H, typename OneHot, int... I>
+__device__ __forceinline__ H shell_sum(const AxisTable<KIND, R>& ax, uint32_t excl, OneHot& onehot,
+                                       std::integer_sequence<int, I...>) {
+    return ((H)0 + ... + vector_increment<KIND, R, FIRST + I, EXCL, H>(ax, excl, onehot));
 }
 
-template <int KIND, int R, int K, typename OneHot>
-__device__ __forceinline__ uint64_t shell_histogram(const AxisTable<KIND, R>& ax, uint32_t excl, OneHot& onehot) {
+template <int KIND, int R, int K, bool EXCL, typename H, typename OneHot>
+__device__ __forceinline__ H shell_histogram(const AxisTable<KIND, R>& ax, uint32_t excl, OneHot& onehot) {
     constexpr int first = ShellsOf<KIND>::table.first[K];
     constexpr int z = ShellsOf<KIND>::table.z[K];
-    return shell_sum<KIND, R, first>(ax, excl, onehot, std::make_integer_sequence<int, z>{});
+    return shell_sum<KIND, R, first, EXCL, H>(ax, excl, onehot, std::make_integer_sequence<int, z>{});
 }
 
-template <int KIND, int R, int MX, typename OneHot, int... K>
-__device__ __forceinline__ void all_shells(const AxisTable<KIND, R>& ax, uint32_t excl, OneHot& onehot,
-                                           uint64_t (&h)[MX], int M, std::integer_sequence<int, K...>) {
-    ((h[K] = (K < M) ? shell_histogram<KIND, R, K>(ax, excl, onehot) : 0ull), ...);
+template <int KIND, int R, int MX, bool EXCL, typename H, typename OneHot, int... K>
+__device__ __forceinline__ void all_shells(const AxisTable<KIND, R>& ax, uint32_t excl, OneHot& onehot, H (&h)[MX],
+                                           int M, std::integer_sequence<int, K...>) {
+    ((h[K] = (K < M) ? shell_histogram<KIND, R, K, EXCL, H>(ax, excl, onehot) : (H)0), ...);
 }
 
-// Neighbour histogram of one site for shells 1..M (M <= MX): h[k] holds 8-bit counts per species
-// (field y at bits 8y..8y+7; Z_k <= 24 fits), skipping the neighbour equal to `excl`.
-// `onehot(n)` returns 1 << (8 * species(n)), or 0 for a site that must not be counted.
+// Neighbour histogram of the site at half-unit position (X, Y, Z) for shells 1..M (M <= MX):
+// h[k] holds 8-bit counts per species (field y at bits 8y..8y+7; Z_k <= 24 fits); with EXCL the
+// neighbour `excl` is skipped.  `onehot(n)` returns 1 << (8 * species(n)) (type H), or 0 for a site
+// that must not be counted.
+template <int KIND, int MX, bool EXCL, typename H, typename OneHot>
+__device__ __forceinline__ void neighbour_histogram_at(const Geo& g, int X, int Y, int Z, uint32_t excl,
+                                                       OneHot onehot, H (&h)[MX], int M) {
+    constexpr int R = shell_reach<KIND, MX>();
+    AxisTable<KIND, R> ax;
+    ax.build(g, X, Y, Z);
+    all_shells<KIND, R, MX, EXCL, H>(ax, excl, onehot, h, M, std::make_integer_sequence<int, MX>{});
+}
+
+// The same for a site index, 64-bit fields, skipping `excl`.
 template <int KIND, int MX, typename OneHot>
 __device__ __forceinline__ void neighbour_histogram_upto(const Geo& g, uint32_t site, uint32_t excl, OneHot onehot,
                                                          uint64_t (&h)[MX], int M) {
-    constexpr int R = shell_reach<KIND, MX>();
     int X, Y, Z;
     site_coords<KIND>(g, site, X, Y, Z);
-    AxisTable<KIND, R> ax;
-    ax.build(g, X, Y, Z);
-    all_shells<KIND, R, MX>(ax, excl, onehot, h, M, std::make_integer_sequence<int, MX>{});
+    neighbour_histogram_at<KIND, MX, true, uint64_t>(g, X, Y, Z, excl, onehot, h, M);
 }
 
+// Full histogram (no site skipped) of a site index, 64-bit fields, compile-time shell count.
 template <int KIND, int M, typename OneHot>
 __device__ __forceinline__ void neighbour_histogram(const Geo& g, uint32_t site, uint32_t excl, OneHot onehot,
                                                     uint64_t (&h)[M]) {
-    neighbour_histogram_upto<KIND, M>(g, site, excl, onehot, h, M);
+    int X, Y, Z;
+    site_coords<KIND>(g, site, X, Y, Z);
+    (void)excl;
+    neighbour_histogram_at<KIND, M, false, uint64_t>(g, X, Y, Z, 0u, onehot, h, M);
 }
 
 __device__ __forceinline__ int hist_field(uint64_t h, int y) { return (int)((h >> (8 * y)) & 0xFFu); }

@@ -319,6 +319,7 @@ struct ChainCtx {
     bool use_filter;
     float rel;   // (E + 4) 2^-23: relative part of the FP32 key bound
     int qcap;    // candidate slots in shared memory
+    int r2max;   // |d|^2 of shell M, half units^2
     bool pos_thr;            // threshold > 0
     float thr_lo, thr_hi;    // binary32 neighbours of the threshold
 };
@@ -338,6 +339,7 @@ __device__ void chain_setup(const ChainDesc& d, ChainSmem& m, ChainShared& sh, C
     c.seed_hi = (uint32_t)(d.seed >> 32);
     c.rel = (float)(c.E + 4) * kTwoUlp;
     c.qcap = d.qcap;
+    c.r2max = c_shells[KIND].radius2[d.M - 1];
     c.pos_thr = d.threshold > 0.0;
     {
         float f = (float)d.threshold;
@@ -415,6 +417,18 @@ __device__ void chain_setup(const ChainDesc& d, ChainSmem& m, ChainShared& sh, C
     c.use_filter = sh.use_filter != 0;
 }
 
+// Minimum-image squared length (half units^2) of a displacement between two sites of the cell.
+__device__ __forceinline__ int min_image_r2(int dx, int dy, int dz, const Geo& g) {
+    const int PX = 2 * g.Lx, PY = 2 * g.Ly, PZ = 2 * g.Lz;
+    dx = dx < 0 ? -dx : dx;
+    dy = dy < 0 ? -dy : dy;
+    dz = dz < 0 ? -dz : dz;
+    dx = min(dx, PX - dx);
+    dy = min(dy, PY - dy);
+    dz = min(dz, PZ - dz);
+    return dx * dx + dy * dy + dz * dz;
+}
+
 // ---- 1. score candidates k in [k_begin, k_end) of step `step`; queue the ones that may matter ----
 // Returns this thread's minimum of the upper bounds (null moves count as 0).
 template <int KIND, int BITS>
@@ -441,11 +455,38 @@ __device__ float score_range(const ChainDesc& d, ChainSmem& m, ChainShared& sh, 
             }
             continue;
         }
-        uint64_t ha[MX], hb[MX], gb[MX];
-        neighbour_histogram_upto<KIND, MX>(c.g, a, b, onehot, ha, M);
-        neighbour_histogram_upto<KIND, MX>(c.g, b, a, onehot, hb, M);
+        // Histograms of both sites.  b can be a shell neighbour of a only when their minimum-image
+        // squared distance is at most r2 of shell M; otherwise no neighbour needs skipping.  With at
+        // most four species the 8-bit fields fit one 32-bit word.
+        int Xa, Ya, Za, Xb, Yb, Zb;
+        site_coords<KIND>(c.g, a, Xa, Ya, Za);
+        site_coords<KIND>(c.g, b, Xb, Yb, Zb);
+        const bool near = min_image_r2(Xb - Xa, Yb - Ya, Zb - Za, c.g) <= c.r2max;
+        uint64_t gb[MX];
+        if (c.S <= 4) {
+            auto onehot32 = [&](uint32_t n) -> uint32_t { return 1u << (8 * load_species<BITS>(m.types, n)); };
+            uint32_t ha[MX], hb[MX];
+            if (near) {
+                neighbour_histogram_at<KIND, MX, true, uint32_t>(c.g, Xa, Ya, Za, b, onehot32, ha, M);
+                neighbour_histogram_at<KIND, MX, true, uint32_t>(c.g, Xb, Yb, Zb, a, onehot32, hb, M);
+            } else {
+                neighbour_histogram_at<KIND, MX, false, uint32_t>(c.g, Xa, Ya, Za, 0u, onehot32, ha, M);
+                neighbour_histogram_at<KIND, MX, false, uint32_t>(c.g, Xb, Yb, Zb, 0u, onehot32, hb, M);
+            }
 #pragma unroll
-        for (int k = 0; k < MX; ++k) gb[k] = pack_g(ha[k], hb[k]);
+            for (int k = 0; k < MX; ++k) gb[k] = pack_g(ha[k], hb[k]);
+        } else {
+            uint64_t ha[MX], hb[MX];
+            if (near) {
+                neighbour_histogram_at<KIND, MX, true, uint64_t>(c.g, Xa, Ya, Za, b, onehot, ha, M);
+                neighbour_histogram_at<KIND, MX, true, uint64_t>(c.g, Xb, Yb, Zb, a, onehot, hb, M);
+            } else {
+                neighbour_histogram_at<KIND, MX, false, uint64_t>(c.g, Xa, Ya, Za, 0u, onehot, ha, M);
+                neighbour_histogram_at<KIND, MX, false, uint64_t>(c.g, Xb, Yb, Zb, 0u, onehot, hb, M);
+            }
+#pragma unroll
+            for (int k = 0; k < MX; ++k) gb[k] = pack_g(ha[k], hb[k]);
+        }
         float lo = -CUDART_INF_F, hi = CUDART_INF_F;
         if (c.use_filter) {
             float Dt, err;
