@@ -56,7 +56,9 @@ typedef enum {
     HEA_ENOMEM = 2,    /* problem does not fit the on-chip (shared-memory) budget of a kernel */
     HEA_ECUDA = 3,     /* a CUDA runtime call failed (no device, launch error) */
     HEA_ETIMEOUT = 4,  /* a search stopped at its time budget (reported in hea_search_result) */
-    HEA_EMISMATCH = 5  /* reserved: internal consistency check failed */
+    HEA_EMISMATCH = 5, /* reserved (no call returns it) */
+    HEA_ESYNC = 6      /* a cooperative search stopped because a wait for another CTA's records ran out
+                          (reported in hea_search_result) */
 } hea_status;
 
 typedef enum { HEA_FCC = 0, HEA_BCC = 1 } hea_kind;
@@ -154,8 +156,13 @@ typedef struct {
     int32_t group_size;   /* multi-accept: candidate k belongs to group k / group_size (0 = one group of K) */
     int32_t group_top;    /* multi-accept: only the group_top best eligible candidates (by (D, k)) of each
                              group enter the walk (0 = all eligible candidates) */
-    int32_t reserved;     /* must be 0 */
+    int32_t sync_wait_us; /* cooperative search: limit of each wait for another CTA's records, in
+                             microseconds (0 = 2,000,000); ignored by the other searches */
     int64_t timeout_us;   /* wall-clock budget measured on the device, 0 = none */
+    int32_t test_withhold_cta; /* testing aid of the cooperative search: 1 + the index of a CTA that
+                                  never publishes its records, so that the others' bounded waits run
+                                  out and the search ends with HEA_ESYNC (0 = none; must be 0 elsewhere) */
+    int32_t reserved;     /* must be 0 */
 } hea_search_params;
 
 /* Written by the search on the device (device or host-mapped pinned memory). */
@@ -164,7 +171,8 @@ typedef struct {
     int64_t trials;    /* candidates scored = steps * K */
     int64_t accepted;  /* swaps applied */
     int32_t depth;     /* depth counter at exit */
-    int32_t status;    /* HEA_OK, or HEA_ETIMEOUT when the time budget ended the search */
+    int32_t status;    /* HEA_OK; HEA_ETIMEOUT when the time budget ended the search; HEA_ESYNC when a
+                          cooperative search stopped because a wait for another CTA ran out */
     double f2;         /* F^2 of the final state (canonical order) */
     double f;          /* sqrt(F^2) */
 } hea_search_result;
@@ -203,18 +211,20 @@ hea_status hea_search_batch(const void* plan_host, const void* plan_dev, void* s
 /*
  * Cooperative search: one chain run by `ctas` co-resident CTAs, one per SM, each holding a copy
  * of the cell in shared memory.  The K candidates of a step are split into ctas equal slices;
- * each CTA scores its slice, the CTAs exchange their best candidates through `workspace`
- * behind a grid barrier, and every CTA applies the same accepted swaps.  Results are those of
- * hea_search with the same parameters:
+ * each CTA scores its slice and publishes its best candidates (records) through `workspace`, every
+ * CTA reads all records once each CTA's tag for the step is visible, and every CTA applies the same
+ * accepted swaps.  Results are those of hea_search with the same parameters:
  *   best-of-K (accept_mode 0): identical to hea_search for any K;
- *   multi-accept (accept_mode 1): requires group_size = K / ctas and 1 <= group_top <= 4, and is
- *   then identical to hea_search with those group parameters.
+ *   multi-accept (accept_mode 1): requires group_size = K / ctas, 1 <= group_top <= 4 and
+ *   ctas * group_top <= 640, and is then identical to hea_search with those group parameters.
  *   workspace        device memory of at least hea_search_coop_workspace_bytes(ctas) bytes,
- *                    16-byte aligned, owned by the caller; its first 64 bytes are zeroed on
- *                    `stream` before the launch; calls that share a workspace must not overlap
+ *                    16-byte aligned, owned by the caller; its first (header and tag) bytes are
+ *                    zeroed on `stream` before the launch; calls that share a workspace must not
+ *                    overlap
  * Errors: HEA_EINVAL for bad parameters or a short workspace; HEA_ENOMEM when `ctas` CTAs with
- * this cell cannot all be resident (see hea_search_coop_max_ctas).  A grid barrier that waits
- * longer than 2 s ends the search with status HEA_ETIMEOUT in the result.
+ * this cell cannot all be resident (see hea_search_coop_max_ctas).  Each wait for another CTA's
+ * records is bounded (params->sync_wait_us, default 2 s); a wait that runs out ends the search with
+ * status HEA_ESYNC in the result (the state written back is the one before the unfinished step).
  */
 size_t hea_search_coop_workspace_bytes(int ctas);
 /* Most CTAs that can be co-resident for this problem with `ctas`-way splitting (0 on error). */
@@ -231,16 +241,18 @@ hea_status hea_search_coop(const hea_lattice* lat, const hea_objective* obj, con
  * exchange area of the cooperative search lives in a fixed array of HEA_NOALLOC_SCRATCH_BYTES
  * bytes inside the library's device image, held by every GPU that loads the library until the
  * process exits.  Nothing is allocated.
- *   - ctas must need at most HEA_NOALLOC_SCRATCH_BYTES of exchange area (up to 512 CTAs);
- *     larger requests return HEA_EINVAL before any launch.
+ *   - ctas must be at most HEA_NOALLOC_MAX_CTAS; larger requests return HEA_EINVAL before any
+ *     launch.
  *   - The array is shared by every call on a device and keeps the last call's contents; each call
- *     clears the barrier header on `stream` before launching.  Calls that overlap on the GPU race
- *     on the array: serialise them.
- *   - The first call on a device (with that device current) looks up the array's address once;
- *     make that first call before any stream capture.
+ *     clears the header and tag words on `stream` before launching.  Calls that overlap on the GPU
+ *     race on the array: serialise them.
+ *   - The first call on a device (with that device current) looks up the array's address once per
+ *     CUDA context; make that first call before any stream capture.  After a device reset the next
+ *     call looks the address up again.
  * Other arguments, results and errors: as hea_search_coop.
  */
-#define HEA_NOALLOC_SCRATCH_BYTES 307200
+#define HEA_NOALLOC_MAX_CTAS 512
+#define HEA_NOALLOC_SCRATCH_BYTES 344064
 hea_status hea_search_coop_noalloc(const hea_lattice* lat, const hea_objective* obj, const hea_search_params* params,
                                    int ctas, uint8_t* types, int32_t* counts, hea_search_result* result, void* stream);
 

@@ -85,12 +85,14 @@ hea_status check_params(const hea_lattice* lat, const hea_search_params* p) {
     if (p->group_size < 0 || p->group_top < 0) return fail(HEA_EINVAL, "negative group_size or group_top");
     if (!(p->threshold >= 0.0) || !std::isfinite(p->threshold)) return fail(HEA_EINVAL, "threshold must be finite and >= 0");
     if (p->reserved != 0) return fail(HEA_EINVAL, "reserved field must be 0");
+    if (p->sync_wait_us < 0) return fail(HEA_EINVAL, "sync_wait_us < 0");
+    if (p->test_withhold_cta < 0) return fail(HEA_EINVAL, "test_withhold_cta < 0");
     if (p->timeout_us < 0) return fail(HEA_EINVAL, "timeout_us < 0");
     (void)lat;
     return ok();
 }
 
-// Chooses 8- or 4-bit species storage so that the chain's shared memory (the cell plus `qcap`
+// Chooses 8-, 4- or (at most 4 species) 2-bit species storage so that the chain's shared memory (the cell plus `qcap`
 // candidate slots) fits one CTA, preferring room for the pairwise multi-accept walk over ranked
 // lists of up to `walk_cap` candidates.
 hea_status place_chain(const hea_lattice* lat, int S, const hea_search_params* p, int qcap, hea::ChainDesc* d,
@@ -102,7 +104,8 @@ hea_status place_chain(const hea_lattice* lat, int S, const hea_search_params* p
     // The pairwise walk keeps site positions as int16 half-unit coordinates.
     if (2 * std::max(lat->Lx, std::max(lat->Ly, lat->Lz)) > 32767) cap = 0;
     for (int pc : {cap, 0}) {
-        for (int bits : {8, 4}) {
+        for (int bits : {8, 4, 2}) {
+            if (bits == 2 && S > 4) continue;
             const hea::ChainLayout L = hea::chain_layout((int)lat->N, lat->M, S, qcap, bits, p->accept_mode, pc);
             if (L.total + 2048 <= hea::kSearchSmemLimit) {
                 d->bits = bits;
@@ -118,11 +121,12 @@ hea_status place_chain(const hea_lattice* lat, int S, const hea_search_params* p
 }
 
 // Cooperative chain: K = ctas * Kc; multi-accept needs group_size = Kc and 1 <= group_top <= 4.
-hea_status check_coop(const hea_search_params* p, int ctas, int* qcap) {
+hea_status check_coop(const hea_search_params* p, int ctas, int* Kc_out, int* top_out) {
     if (ctas < 1 || ctas > 65535) return fail(HEA_EINVAL, "ctas = %d outside [1, 65535]", ctas);
     if (p->K % ctas != 0) return fail(HEA_EINVAL, "K = %d is not a multiple of ctas = %d", p->K, ctas);
     const int Kc = p->K / ctas;
-    if (Kc > hea::kMaxK) return fail(HEA_EINVAL, "K / ctas = %d exceeds %d", Kc, hea::kMaxK);
+    const int most = (p->accept_mode == 1) ? hea::kCoopMaxKc : hea::kMaxK;
+    if (Kc > most) return fail(HEA_EINVAL, "K / ctas = %d exceeds %d", Kc, most);
     int top = 1;
     if (p->accept_mode == 1) {
         if (p->group_size != Kc)
@@ -130,8 +134,12 @@ hea_status check_coop(const hea_search_params* p, int ctas, int* qcap) {
         if (p->group_top < 1 || p->group_top > hea::kCoopMaxTop)
             return fail(HEA_EINVAL, "cooperative multi-accept needs 1 <= group_top <= %d", hea::kCoopMaxTop);
         top = p->group_top;
+        if (ctas * top > hea::kPairWalkMax)
+            return fail(HEA_EINVAL, "cooperative multi-accept merges ctas * group_top = %d records; at most %d", ctas * top,
+                        hea::kPairWalkMax);
     }
-    *qcap = Kc > ctas * top ? Kc : ctas * top;
+    *Kc_out = Kc;
+    *top_out = top;
     return ok();
 }
 
@@ -149,6 +157,41 @@ void fill_params(const hea_search_params* p, hea::ChainDesc* d) {
     d->timeout_ns = p->timeout_us * 1000;
     d->seed = p->seed;
     d->threshold = p->threshold;
+    d->wait_ns = (p->sync_wait_us > 0 ? (int64_t)p->sync_wait_us : 2000000ll) * 1000;
+    d->withhold = p->test_withhold_cta;
+}
+
+// Cooperative chain: the chain arrays, the fixed-point tables and the walk over `nrec` merged
+// records in one CTA's shared memory.  Multi-accept scores a CTA's slice in chunks (the best
+// candidates so far are carried from chunk to chunk), so the candidate slots hold one chunk plus
+// the carried ones: the largest chunk of 1024, 512 or 256 (at most Kc) that fits, with the widest
+// species storage (8, 4, or for at most 4 species 2 bits per site).  Best-of-K scores the slice at
+// once.
+hea_status place_coop(const hea_lattice* lat, int S, const hea_search_params* p, int Kc, int ctas, int top,
+                      hea::ChainDesc* d) {
+    const int nrec = ctas * top;
+    const int chunks[3] = {1024, 512, 256};
+    for (int ci = 0; ci < 3; ++ci) {
+        const int chunk = (p->accept_mode == 1) ? std::min(Kc, chunks[ci]) : Kc;
+        if (p->accept_mode == 1 && ci > 0 && chunk == std::min(Kc, chunks[ci - 1])) continue;
+        const int qcap = std::max((p->accept_mode == 1) ? chunk + top : chunk, nrec);
+        for (int bits : {8, 4, 2}) {
+            if (bits == 2 && S > 4) continue;
+            const hea::ChainLayout L = hea::coop_layout((int)lat->N, lat->M, S, qcap, bits, p->accept_mode, nrec);
+            if (L.total + 2048 <= hea::kSearchSmemLimit) {
+                d->bits = bits;
+                d->smem_bytes = L.total;
+                d->qcap = qcap;
+                d->pair_cap = 0;
+                d->nrec = nrec;
+                d->chunk = chunk;
+                return ok();
+            }
+        }
+        if (p->accept_mode != 1) break;
+    }
+    return fail(HEA_ENOMEM, "cell of %lld sites with %d merged records does not fit one CTA's shared memory",
+                (long long)lat->N, nrec);
 }
 
 // Plan = header + descriptors sorted by lattice kind (FCC first), then largest work first.
@@ -181,6 +224,7 @@ const char* hea_status_string(int status) {
         case HEA_ECUDA: return "CUDA error";
         case HEA_ETIMEOUT: return "time budget reached";
         case HEA_EMISMATCH: return "consistency check failed";
+        case HEA_ESYNC: return "a wait for another CTA ran out";
         default: return "unknown status";
     }
 }
@@ -276,6 +320,7 @@ hea_status hea_search(const hea_lattice* lat, const hea_objective* obj, const he
     st = check_params(lat, params);
     if (st != HEA_OK) return st;
     if (params->K > hea::kMaxK) return fail(HEA_EINVAL, "K = %d exceeds %d for a single-CTA chain", params->K, hea::kMaxK);
+    if (params->test_withhold_cta != 0) return fail(HEA_EINVAL, "test_withhold_cta applies to cooperative searches only");
     hea::ChainDesc d;
     fill_desc(lat, obj, &d);
     fill_params(params, &d);
@@ -306,6 +351,8 @@ hea_status hea_search_batch_plan(int n, const hea_lattice* const* lats, const he
         hea_status st = check_objective(lats[c], &objs[c]);
         if (st == HEA_OK) st = check_params(lats[c], &params[c]);
         if (st == HEA_OK && params[c].K > hea::kMaxK) st = fail(HEA_EINVAL, "K = %d exceeds %d", params[c].K, hea::kMaxK);
+        if (st == HEA_OK && params[c].test_withhold_cta != 0)
+            st = fail(HEA_EINVAL, "test_withhold_cta applies to cooperative searches only");
         if (st == HEA_OK) {
             fill_desc(lats[c], &objs[c], &descs[c]);
             fill_params(&params[c], &descs[c]);
@@ -362,13 +409,12 @@ int hea_search_coop_max_ctas(const hea_lattice* lat, const hea_objective* obj, c
                              int ctas) {
     if (!lat) return 0;
     if (check_objective(lat, obj) != HEA_OK || check_params(lat, params) != HEA_OK) return 0;
-    int qcap = 0;
-    if (check_coop(params, ctas, &qcap) != HEA_OK) return 0;
+    int Kc = 0, top = 1;
+    if (check_coop(params, ctas, &Kc, &top) != HEA_OK) return 0;
     hea::ChainDesc d;
     fill_desc(lat, obj, &d);
     fill_params(params, &d);
-    if (place_chain(lat, obj->S, params, qcap, &d, ctas * (params->accept_mode == 1 ? params->group_top : 1)) != HEA_OK)
-        return 0;
+    if (place_coop(lat, obj->S, params, Kc, ctas, top, &d) != HEA_OK) return 0;
     return (d.kind == HEA_FCC) ? hea::coop_max_ctas_fcc(d) : hea::coop_max_ctas_bcc(d);
 }
 
@@ -380,17 +426,18 @@ hea_status hea_search_coop(const hea_lattice* lat, const hea_objective* obj, con
     if (st != HEA_OK) return st;
     st = check_params(lat, params);
     if (st != HEA_OK) return st;
-    int qcap = 0;
-    st = check_coop(params, ctas, &qcap);
+    int Kc = 0, top = 1;
+    st = check_coop(params, ctas, &Kc, &top);
     if (st != HEA_OK) return st;
     if (workspace_bytes < hea::coop_workspace_bytes(ctas))
         return fail(HEA_EINVAL, "workspace of %zu bytes is smaller than the %zu needed", workspace_bytes,
                     hea::coop_workspace_bytes(ctas));
     if (reinterpret_cast<uintptr_t>(workspace) % 16 != 0) return fail(HEA_EINVAL, "workspace is not 16-byte aligned");
+    if (params->test_withhold_cta > ctas) return fail(HEA_EINVAL, "test_withhold_cta names a CTA beyond ctas");
     hea::ChainDesc d;
     fill_desc(lat, obj, &d);
     fill_params(params, &d);
-    st = place_chain(lat, obj->S, params, qcap, &d, ctas * (params->accept_mode == 1 ? params->group_top : 1));
+    st = place_coop(lat, obj->S, params, Kc, ctas, top, &d);
     if (st != HEA_OK) return st;
     const int most = (d.kind == HEA_FCC) ? hea::coop_max_ctas_fcc(d) : hea::coop_max_ctas_bcc(d);
     if (most < 1) return fail(HEA_ECUDA, "no CUDA device for a cooperative launch");

@@ -206,13 +206,21 @@ struct AxisTable {
 };
 
 // ------------------------------------------------------------------------------------------------
-// Species storage in shared memory: 8 bits per site, or 4 bits per site (two sites per byte,
-// even site in the low nibble) for cells that do not fit at 8 bits.
+// Species storage in shared memory: 8, 4 or 2 bits per site (2 only for at most 4 species); with
+// fewer than 8 bits, site i sits in bits BITS * (i mod 8/BITS) of byte i / (8/BITS).
 // ------------------------------------------------------------------------------------------------
+template <int BITS>
+struct Packing {
+    static constexpr uint32_t per = 8 / BITS;                  // sites per byte
+    static constexpr int lg = BITS == 8 ? 0 : (BITS == 4 ? 1 : 2);
+    static constexpr uint32_t mask = (1u << BITS) - 1u;
+};
+
 template <int BITS>
 __device__ __forceinline__ int load_species(const uint8_t* s, uint32_t i) {
     if (BITS == 8) return s[i];
-    return (s[i >> 1] >> ((i & 1u) << 2)) & 0xF;
+    using P = Packing<BITS>;
+    return (s[i >> P::lg] >> ((i & (P::per - 1u)) * BITS)) & P::mask;
 }
 
 template <int BITS>
@@ -220,14 +228,16 @@ __device__ __forceinline__ void store_species(uint8_t* s, uint32_t i, int v) {
     if (BITS == 8) {
         s[i] = (uint8_t)v;
     } else {
-        const uint32_t sh = (i & 1u) << 2;
-        s[i >> 1] = (uint8_t)((s[i >> 1] & ~(0xFu << sh)) | ((uint32_t)v << sh));
+        using P = Packing<BITS>;
+        const uint32_t sh = (i & (P::per - 1u)) * BITS;
+        const uint32_t byte = i >> P::lg;
+        s[byte] = (uint8_t)((s[byte] & ~(P::mask << sh)) | ((uint32_t)v << sh));
     }
 }
 
 template <int BITS>
 __host__ __device__ constexpr uint32_t species_bytes(uint32_t N) {
-    return BITS == 8 ? N : (N + 1) / 2;
+    return BITS == 8 ? N : (BITS == 4 ? (N + 1) / 2 : (N + 3) / 4);
 }
 
 template <int KIND>

@@ -10,7 +10,8 @@ namespace hea {
 
 constexpr int kChainThreads = 256;   // threads of a single-CTA search chain
 constexpr int kCoopThreads = 512;    // threads of each CTA of a cooperative chain
-constexpr int kMaxK = 4096;          // candidates per CTA per step
+constexpr int kMaxK = 4096;          // candidates per CTA per step (cooperative multi-accept: per chunk)
+constexpr int kCoopMaxKc = 1 << 20;  // cooperative multi-accept: candidates per CTA per step
 constexpr int kCoopMaxTop = 4;       // records (best eligible candidates) per CTA per step
 constexpr int kPairWalkMax = 640;    // longest ranked list the pairwise multi-accept walk handles
 constexpr uint32_t kSearchSmemLimit = 227 * 1024;
@@ -18,7 +19,7 @@ constexpr uint32_t kSearchSmemLimit = 227 * 1024;
 // Everything one search chain needs, passed by value (single chain) or from device memory
 // (batched search).  Objective tables are copied in so a launch reads no host memory.
 struct ChainDesc {
-    int32_t kind, Lx, Ly, Lz, M, S, N, bits;  // bits: species storage, 8 or 4 per site
+    int32_t kind, Lx, Ly, Lz, M, S, N, bits;  // bits: species storage, 8, 4 or 2 per site
     int32_t K, accept_mode, depth_limit, max_accept;
     uint32_t chain, step0;
     int32_t depth0, group_size, group_top, ctas;
@@ -36,12 +37,19 @@ struct ChainDesc {
     void* workspace;        // cooperative chain: exchange area (see CoopHeader)
     uint32_t smem_bytes;
     int32_t qcap;           // candidate slots in shared memory
+    int64_t wait_ns;        // cooperative chain: limit of each wait for the other CTAs' records
+    int32_t withhold;       // cooperative chain, testing aid: 1 + index of a CTA that never publishes (0 = none)
+    int32_t nrec;           // cooperative chain: most records merged per step (ctas * records per CTA)
+    int32_t chunk;          // cooperative multi-accept: candidates scored per pass (the slice is scored in chunks)
+    int32_t pad3;
 };
 
 // Shared-memory layout of one search CTA (offsets in bytes from the dynamic smem base).
 struct ChainLayout {
     uint32_t types, cnt, Q, tgt, ca, cb, fa, fb, fQ, fe0, dn, tiny, beta, vec, slot;
     uint32_t qk, qa, qb, qlo, qhi, qD, qkey, qg, order, acc, bitmap, fw;
+    // cooperative chain only: fixed-point coefficient tables, per-slot fixed-point keys, walk data
+    uint32_t fA, fB, qfix, qeps, qflag, walk;
     uint32_t total;
 };
 
@@ -84,7 +92,7 @@ __host__ __device__ inline ChainLayout chain_layout(int N, int M, int S, int qca
     const uint32_t C = (uint32_t)qcap;
     uint32_t o = 0;
     L.types = o;
-    o = align_up(o + (bits == 8 ? (uint32_t)N : (uint32_t)(N + 1) / 2), 16);
+    o = align_up(o + (bits == 8 ? (uint32_t)N : (bits == 4 ? (uint32_t)(N + 1) / 2 : (uint32_t)(N + 3) / 4)), 16);
     L.cnt = o;    o = align_up(o + 4 * E, 16);
     L.Q = o;      o = align_up(o + 8 * E, 16);
     L.tgt = o;    o = align_up(o + 8 * E, 16);
@@ -122,27 +130,65 @@ __host__ __device__ inline ChainLayout chain_layout(int N, int M, int S, int qca
     return L;
 }
 
+// Data of the multi-accept walk of a cooperative chain over at most `nrec` ranked candidates (E
+// entries, rows of Ep = E rounded up to 4): dense count changes int8 [nrec][Ep], sites u32
+// [nrec][2], species u8 [nrec][2], positions int16 [nrec][6], the conflict matrix u32
+// [nrec][ceil(nrec / 32)], two occupancy bitmaps of hashed conventional cells (kCoopCellBits bits
+// each), suspect sites u16 [2 nrec], then one batch of 32: rows float [32][Ws] x 2 (Ws: Ep padded
+// to 4 mod 8), cross terms, their bounds and three prefix-sum tables float [32][33] x 5, keys and
+// bounds float [32] x 2, conflict masks u32 [32] x 2.  The device-side pointers (coop_walk_arrays)
+// follow this order.
+constexpr int kCoopCellBits = 15;
+constexpr uint32_t kCoopCellWords = (1u << kCoopCellBits) / 32u;
+
+__host__ __device__ inline uint32_t coop_walk_bytes(int nrec, int E) {
+    const uint32_t n = (uint32_t)nrec, Ep = ((uint32_t)E + 3u) & ~3u;
+    const uint32_t Ws = (Ep % 8u == 4u) ? Ep : Ep + 4u;   // batch row stride (floats)
+    const uint32_t nw = (n + 31u) / 32u;
+    return align_up(n * Ep, 16) + align_up(8 * n, 16) + align_up(2 * n, 16) + align_up(12 * n, 16) +
+           align_up(4 * n * nw, 16) + 2 * 4 * kCoopCellWords + align_up(4 * n, 16) + 2 * 4 * 32 * Ws +
+           5 * 4 * 32 * 33 + 2 * 4 * 32 + 2 * 4 * 32;
+}
+
+// Shared memory of a cooperative chain: the arrays of a chain (without the single-chain walk
+// data) followed by the fixed-point tables, per-slot keys and the walk data.
+__host__ __device__ inline ChainLayout coop_layout(int N, int M, int S, int qcap, int bits, int accept_mode, int nrec) {
+    ChainLayout L = chain_layout(N, M, S, qcap, bits, 0, 0);
+    const uint32_t E = (uint32_t)(M * S * S), C = (uint32_t)qcap;
+    uint32_t o = L.total;
+    L.fA = o;     o = align_up(o + 8 * E, 16);
+    L.fB = o;     o = align_up(o + 8 * E, 16);
+    L.qfix = o;   o = align_up(o + 8 * C, 16);
+    L.qeps = o;   o = align_up(o + 8 * C, 16);
+    L.qflag = o;  o = align_up(o + 4 * C, 16);
+    L.walk = o;
+    if (accept_mode == 1) o = align_up(o + coop_walk_bytes(nrec, (int)E), 16);
+    L.total = o;
+    return L;
+}
+
 // Exchange area of a cooperative chain (caller-provided device memory): a header, then for each
-// of two step parities and each CTA, a count and up to kCoopMaxTop candidate records.
+// of two step parities and each CTA a tag word, then for each parity and CTA up to kCoopMaxTop
+// candidate records.  CTA r publishes step s (counted from 0 in each launch) by writing its records
+// and then, with release semantics, the tag ((s + 1) << 32) | (stop << 16) | count; the others
+// read the records once they see that tag (acquire).  Only CTA 0 sets `stop` (time budget spent),
+// so every CTA takes the same stop decision for the same step.
 struct CoopHeader {
-    unsigned long long arrive;  // grid barrier: arrivals so far
-    int32_t stop;               // set by CTA 0 before arriving when the time budget is spent
-    int32_t error;              // a barrier wait ran out
-    int32_t pad[12];
+    int32_t error;              // a wait for another CTA's records ran out
+    int32_t pad[15];
 };
 
 struct CoopRecord {
-    double D;        // key: exact, or a point inside [lo, hi]
-    float lo, hi;    // bounds on the key from the FP32 estimate
-    uint32_t k, a, b;
-    int32_t pad;
+    double D;        // binary64 key (best-of-K: always; multi-accept: when flags & 1)
+    float lo, hi;    // FP32 interval around the key (multi-accept)
+    uint32_t k, a, b, flags;
     uint64_t g[5];   // per-shell swap vectors (biased bytes)
 };
 
 // Byte offsets inside the exchange area of a chain of `ctas` CTAs.
-__host__ __device__ inline size_t coop_counts_offset() { return sizeof(CoopHeader); }
+__host__ __device__ inline size_t coop_tags_offset() { return sizeof(CoopHeader); }
 __host__ __device__ inline size_t coop_records_offset(int ctas) {
-    return (coop_counts_offset() + 2 * sizeof(int32_t) * (size_t)ctas + 63) / 64 * 64;
+    return (coop_tags_offset() + 2 * sizeof(unsigned long long) * (size_t)ctas + 63) / 64 * 64;
 }
 __host__ __device__ inline size_t coop_workspace_bytes(int ctas) {
     return coop_records_offset(ctas) + 2 * (size_t)ctas * kCoopMaxTop * sizeof(CoopRecord);

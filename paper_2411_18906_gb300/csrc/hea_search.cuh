@@ -14,10 +14,8 @@
 //   3. best-of-K: argmin over (D, k); multi-accept: eligible candidates ranked by (D, k) and walked
 //      by one warp with a neighbourhood bitmap and a re-check against the running counts;
 //   4. the accepted swap(s) update species, counts and coefficients in place.
-// One CTA runs a chain (run_chain), or a grid of CTAs cooperates on one chain (run_coop_chain):
-// each CTA scores a slice of the K candidates, the CTAs exchange their best candidates through
-// global memory behind a grid barrier, and every CTA applies the same accepted swaps to its own
-// copy of the cell.
+// One CTA runs a chain (run_chain); the cooperative chain over a grid of CTAs (hea_coop.cuh)
+// reuses the scoring and the exact keys.
 #pragma once
 #include <cstdint>
 #include <cuda_runtime.h>
@@ -50,6 +48,15 @@ struct ChainShared {
     int walk_done;   // walk: max_accept reached
     uint32_t taken[kPairWalkMax / 32];   // walk: accepted set of the ranked list
     float umin;      // min over candidates of the upper bound on D
+    // cooperative chain
+    int fixF, fixFa;         // fixed-point scales of the step's b coefficients and of the a coefficients
+    int n_amb;               // candidates whose order against the current winner the intervals leave open
+    int sync_fail;           // a wait for another CTA's records ran out
+    int pub_stop;            // stop bit of CTA 0's record for this step
+    int n_pairs;             // conflicting candidate pairs found for the walk
+    unsigned long long maxb; // max |b| over the entries (binary64 bits)
+    unsigned int wmax;       // walk: bound on the running |b| (binary32 bits)
+    long long red_l[32];
     int64_t steps;
     int64_t accepted;
     uint64_t t0;
@@ -277,8 +284,17 @@ struct ChainSmem {
     uint64_t* qg;
     float* fw;
     uint32_t *order, *acc, *bitmap;
+    long long *fA, *fB, *qfix, *qeps;
+    uint32_t* qflag;
+    uint8_t* walk;
 
     __device__ ChainSmem(uint8_t* smem, const ChainLayout& L) {
+        fA = reinterpret_cast<long long*>(smem + L.fA);
+        fB = reinterpret_cast<long long*>(smem + L.fB);
+        qfix = reinterpret_cast<long long*>(smem + L.qfix);
+        qeps = reinterpret_cast<long long*>(smem + L.qeps);
+        qflag = reinterpret_cast<uint32_t*>(smem + L.qflag);
+        walk = smem + L.walk;
         types = smem + L.types;
         cnt = reinterpret_cast<int32_t*>(smem + L.cnt);
         Q = reinterpret_cast<double*>(smem + L.Q);
@@ -326,7 +342,7 @@ struct ChainCtx {
 
 // ---- set-up: species (validated against S), counts, coefficients, shell vectors ----------------
 template <int KIND, int BITS>
-__device__ void chain_setup(const ChainDesc& d, ChainSmem& m, ChainShared& sh, ChainCtx& c) {
+__device__ void chain_setup(const ChainDesc& d, ChainSmem& m, ChainShared& sh, ChainCtx& c, bool clear_bitmap = true) {
     const int tid = threadIdx.x, T = blockDim.x;
     c.g = make_geo(KIND, d.Lx, d.Ly, d.Lz);
     c.M = d.M;
@@ -368,11 +384,16 @@ __device__ void chain_setup(const ChainDesc& d, ChainSmem& m, ChainShared& sh, C
             m.types[i] = v;
         }
     } else {
-        for (uint32_t i = tid; i < (N + 1) / 2; i += T) {
-            const uint8_t v0 = d.types[2 * i];
-            const uint8_t v1 = (2 * i + 1 < N) ? d.types[2 * i + 1] : 0;
-            if (v0 >= S || v1 >= S) sh.bad = 1;
-            m.types[i] = (uint8_t)((v0 & 0xF) | ((v1 & 0xF) << 4));
+        constexpr uint32_t per = 8 / BITS;
+        for (uint32_t i = tid; i < species_bytes<BITS>(N); i += T) {
+            uint32_t packed = 0;
+#pragma unroll
+            for (uint32_t j = 0; j < per; ++j) {
+                const uint8_t v = (per * i + j < N) ? d.types[per * i + j] : 0;
+                if (v >= S) sh.bad = 1;
+                packed |= (uint32_t)(v & ((1u << BITS) - 1u)) << (BITS * j);
+            }
+            m.types[i] = (uint8_t)packed;
         }
     }
     {
@@ -411,7 +432,7 @@ __device__ void chain_setup(const ChainDesc& d, ChainSmem& m, ChainShared& sh, C
         const double bmax = 2.0 * w * Q * (1.0 + (double)d.N / (double)d.n_per[j] + fabs(t));
         if (!(a * zz * zz < 1e30) || !(bmax * zz < 1e30)) sh.use_filter = 0;
     }
-    if (d.accept_mode == 1)
+    if (d.accept_mode == 1 && clear_bitmap)
         for (uint32_t i = tid; i < (N + 31) / 32; i += T) m.bitmap[i] = 0;
     __syncthreads();
     c.use_filter = sh.use_filter != 0;
@@ -976,17 +997,17 @@ static __device__ double exact_key_pending(int M, int S, const int32_t* cnt, con
     return D;
 }
 
-// Replaces the nibble (4-bit storage) or byte of site i; safe against other threads writing other
-// sites of the same word.
+// Replaces the species of site i; safe against other threads writing other sites of the same word.
 template <int BITS>
 __device__ __forceinline__ void store_species_atomic(uint8_t* s, uint32_t i, int v) {
     if (BITS == 8) {
         s[i] = (uint8_t)v;
     } else {
-        const uint32_t byte = i >> 1;
+        using P = Packing<BITS>;
+        const uint32_t byte = i >> P::lg;
         uint32_t* word = reinterpret_cast<uint32_t*>(s + (byte & ~3u));
-        const uint32_t sh = (byte & 3u) * 8 + (i & 1u) * 4;
-        atomicAnd(word, ~(0xFu << sh));
+        const uint32_t sh = (byte & 3u) * 8 + (i & (P::per - 1u)) * BITS;
+        atomicAnd(word, ~(P::mask << sh));
         atomicOr(word, (uint32_t)v << sh);
     }
 }
@@ -1357,11 +1378,7 @@ __device__ __forceinline__ void bookkeeping(const ChainDesc& d, ChainShared& sh,
 template <int BITS>
 __device__ void write_back(const ChainDesc& d, ChainSmem& m, ChainShared& sh, const ChainCtx& c) {
     const uint32_t N = c.N;
-    if (BITS == 8) {
-        for (uint32_t i = threadIdx.x; i < N; i += blockDim.x) d.types[i] = m.types[i];
-    } else {
-        for (uint32_t i = threadIdx.x; i < N; i += blockDim.x) d.types[i] = (uint8_t)load_species<4>(m.types, i);
-    }
+    for (uint32_t i = threadIdx.x; i < N; i += blockDim.x) d.types[i] = (uint8_t)load_species<BITS>(m.types, i);
     for (int e = threadIdx.x; e < c.E; e += blockDim.x) d.counts[e] = m.cnt[e];
     if (threadIdx.x == 0) {
         const int S = c.S;
@@ -1438,150 +1455,10 @@ __device__ void run_chain(const ChainDesc& d, uint8_t* smem, ChainShared& sh) {
     write_back<BITS>(d, m, sh, c);
 }
 
-// ------------------------------------------------------------------------------------------------
-// Cooperative chain: gridDim.x CTAs (all co-resident) share one chain.  CTA r scores candidates
-// [r Kc, (r+1) Kc) with Kc = K / gridDim.x and publishes its best (best-of-K: its argmin;
-// multi-accept: its group_top best eligible, the group being its slice); every CTA merges all
-// published candidates and applies the same accepted swaps to its own copy of the cell.
-// ------------------------------------------------------------------------------------------------
 __device__ __forceinline__ unsigned long long load_acquire(const unsigned long long* p) {
     unsigned long long v;
     asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
     return v;
-}
-
-// Grid barrier on a monotonically increasing arrival counter.  The wait is bounded (2 s of
-// device time); a CTA whose wait runs out records the failure and reports it instead of spinning.
-static __device__ bool grid_barrier(CoopHeader* h, unsigned long long target, ChainShared& sh) {
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        __threadfence();
-        atomicAdd(&h->arrive, 1ull);
-        const uint64_t t0 = globaltimer_ns();
-        bool ok = true;
-        while (load_acquire(&h->arrive) < target) {
-            if (globaltimer_ns() - t0 > 2000000000ull) {
-                ok = false;
-                atomicExch(&h->error, 1);
-                break;
-            }
-            __nanosleep(32);
-        }
-        __threadfence();
-        sh.sync_ok = ok ? 1 : 0;
-    }
-    __syncthreads();
-    return sh.sync_ok != 0;
-}
-
-template <int KIND, int BITS>
-__device__ void run_coop_chain(const ChainDesc& d, uint8_t* smem, ChainShared& sh) {
-    const ChainLayout L = chain_layout(d.N, d.M, d.S, d.qcap, BITS, d.accept_mode, d.pair_cap);
-    ChainSmem m(smem, L);
-    ChainCtx c;
-    chain_setup<KIND, BITS>(d, m, sh, c);
-    const int G = gridDim.x, rank = blockIdx.x, tid = threadIdx.x;
-    const int top = (d.accept_mode == 0) ? 1 : d.group_top;
-    const uint32_t Kc = (uint32_t)(c.K / G);
-    uint8_t* ws = static_cast<uint8_t*>(d.workspace);
-    CoopHeader* hdr = reinterpret_cast<CoopHeader*>(ws);
-    int32_t* counts_ws = reinterpret_cast<int32_t*>(ws + coop_counts_offset());
-    CoopRecord* recs = reinterpret_cast<CoopRecord*>(ws + coop_records_offset(G));
-    if (sh.bad) {   // identical in every CTA: the cell is the same
-        if (rank == 0) report_invalid(d);
-        return;
-    }
-    unsigned long long phase = 0;
-    while (!sh.stop) {
-        const uint32_t step = d.step0 + (uint32_t)sh.steps;
-        const int par = (int)(sh.steps & 1);
-        if (tid == 0) {
-            sh.qn = 0;
-            sh.n_acc = 0;
-            sh.win_q = -1;
-        }
-        __syncthreads();
-        const float my_umin = score_range<KIND, BITS>(d, m, sh, c, step, rank * Kc, (rank + 1) * Kc);
-        int n_pub = 0;
-        if (d.accept_mode == 0) {
-            const float umin = block_min(my_umin, sh);
-            best_of_queue<BITS>(m, sh, c, umin);
-            if (sh.win_q >= 0) {
-                m.order[0] = (uint32_t)sh.win_q;
-                n_pub = 1;
-            }
-        } else {
-            __syncthreads();
-            rank_eligible<BITS>(m, sh, c, sh.qn, (int)Kc, top, true);
-            n_pub = min(sh.n_elig, top);
-        }
-        // Publish this CTA's candidates for the step (double-buffered by step parity).
-        for (int x = tid; x < n_pub; x += blockDim.x) {
-            const uint32_t q = m.order[x];
-            CoopRecord* R = &recs[((size_t)par * G + rank) * kCoopMaxTop + x];
-            R->D = m.qD[q];
-            R->lo = m.qlo[q];
-            R->hi = m.qhi[q];
-            R->k = m.qk[q];
-            R->a = m.qa[q];
-            R->b = m.qb[q];
-            for (int k = 0; k < c.M; ++k) R->g[k] = m.qg[q * c.M + k];
-        }
-        if (tid == 0) {
-            counts_ws[par * G + rank] = n_pub;
-            if (rank == 0 && d.timeout_ns > 0 && (int64_t)(globaltimer_ns() - sh.t0) >= d.timeout_ns)
-                atomicExch(&hdr->stop, 1);
-        }
-        phase += 1;
-        if (!grid_barrier(hdr, phase * (unsigned long long)G, sh)) {
-            if (tid == 0) sh.status = HEA_ETIMEOUT;
-            __syncthreads();
-            break;
-        }
-        // Merge every CTA's published candidates into the local slots.
-        if (tid == 0) sh.qn = 0;
-        __syncthreads();
-        for (int x = tid; x < G * top; x += blockDim.x) {
-            const int r = x / top, i = x % top;
-            if (i >= __ldcg(&counts_ws[par * G + r])) continue;
-            const CoopRecord* R = &recs[((size_t)par * G + r) * kCoopMaxTop + i];
-            const int slot = atomicAdd(&sh.qn, 1);
-            m.qD[slot] = __ldcg(&R->D);
-            m.qlo[slot] = __ldcg(&R->lo);
-            m.qhi[slot] = __ldcg(&R->hi);
-            m.qk[slot] = __ldcg(&R->k);
-            m.qa[slot] = __ldcg(&R->a);
-            m.qb[slot] = __ldcg(&R->b);
-            for (int k = 0; k < c.M; ++k) m.qg[slot * c.M + k] = __ldcg(&R->g[k]);
-        }
-        __syncthreads();
-        if (d.accept_mode == 0) {
-            // Every CTA published its exact argmin: the global argmin over (D, k).
-            if (tid == 0) {
-                int best = -1;
-                for (int q = 0; q < sh.qn; ++q)
-                    if (best < 0 || better(m.qD[q], m.qk[q], m.qD[best], m.qk[best])) best = q;
-                sh.win_q = best;
-            }
-            __syncthreads();
-            const int q = sh.win_q;
-            if (q >= 0) {
-                const uint32_t a = m.qa[q], b = m.qb[q];
-                const bool null_move = (a == b) || load_species<BITS>(m.types, a) == load_species<BITS>(m.types, b);
-                if (eligible(m.qD[q], null_move, c.thr)) apply_slot<BITS>(d, m, sh, c, q);
-            }
-        } else {
-            // The published candidates are eligible; ranking them across CTAs computes exact keys
-            // where intervals from different CTAs overlap.
-            rank_eligible<BITS>(m, sh, c, sh.qn, 0, 0, true);
-            walk<KIND, BITS>(d, m, sh, c, sh.n_elig);
-            after_walk<KIND>(d, m, sh, c);
-        }
-        __syncthreads();
-        const bool timed_out = __ldcg(&hdr->stop) != 0;
-        bookkeeping(d, sh, timed_out);
-    }
-    if (rank == 0) write_back<BITS>(d, m, sh, c);
 }
 
 }  // namespace hea

@@ -15,7 +15,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libhea.so")
 HEADER = os.path.join(os.path.dirname(HERE), "include", "hea.h")
 
-HEA_OK, HEA_EINVAL, HEA_ENOMEM, HEA_ECUDA, HEA_ETIMEOUT, HEA_EMISMATCH = range(6)
+HEA_OK, HEA_EINVAL, HEA_ENOMEM, HEA_ECUDA, HEA_ETIMEOUT, HEA_EMISMATCH, HEA_ESYNC = range(7)
 HEA_FCC, HEA_BCC = 0, 1
 
 _lib = None
@@ -37,7 +37,8 @@ class hea_search_params(ctypes.Structure):
                 ("depth_limit", ctypes.c_int32), ("max_accept", ctypes.c_int32), ("threshold", ctypes.c_double),
                 ("seed", ctypes.c_uint64), ("chain", ctypes.c_uint32), ("step0", ctypes.c_uint32),
                 ("depth0", ctypes.c_int32), ("group_size", ctypes.c_int32), ("group_top", ctypes.c_int32),
-                ("reserved", ctypes.c_int32), ("timeout_us", ctypes.c_int64)]
+                ("sync_wait_us", ctypes.c_int32), ("timeout_us", ctypes.c_int64), ("test_withhold_cta", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
 
 
 class hea_search_result(ctypes.Structure):
@@ -184,9 +185,9 @@ def hea_delta_swap(lat, obj, types, counts, pairs, K, key, dcounts=None, stream=
 
 
 def search_params(K, max_steps, accept_mode=0, depth_limit=0, max_accept=0, threshold=0.0, seed=1, chain=0,
-                  step0=0, depth0=0, group_size=0, group_top=0, timeout_us=0):
+                  step0=0, depth0=0, group_size=0, group_top=0, timeout_us=0, sync_wait_us=0, test_withhold_cta=0):
     return hea_search_params(K, accept_mode, max_steps, depth_limit, max_accept, threshold, seed, chain, step0,
-                             depth0, group_size, group_top, 0, timeout_us)
+                             depth0, group_size, group_top, sync_wait_us, timeout_us, test_withhold_cta, 0)
 
 
 def hea_search(lat, obj, params, types, counts, result, stream=None):

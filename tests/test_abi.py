@@ -80,7 +80,14 @@ def test_validation_before_launch(L):
 
 
 def test_search_rejects_cells_beyond_shared_memory(L):
-    lat = hea.hea_build_lattice(hea.HEA_FCC, 50, 50, 50, 3)       # 500,000 sites
+    # 5 species need 4 bits per site: 500,000 sites take 250,000 bytes, beyond one CTA's shared memory
+    lat = hea.hea_build_lattice(hea.HEA_FCC, 50, 50, 50, 3)
+    N = lat.N
+    obj = hea.Objective([N // 5] * 5, np.ones(3), np.zeros((3, 5, 5)))
+    assert _status(hea.hea_search, lat, obj, hea.search_params(256, 10), FakePtr(), FakePtr(), FakePtr(), 0) \
+        == hea.HEA_ENOMEM
+    # 4 species fit 2 bits per site, up to about 900,000 sites; 953,312 do not fit
+    lat = hea.hea_build_lattice(hea.HEA_FCC, 62, 62, 62, 3)
     N = lat.N
     obj = hea.Objective([N // 4] * 4, np.ones(3), np.zeros((3, 4, 4)))
     assert _status(hea.hea_search, lat, obj, hea.search_params(256, 10), FakePtr(), FakePtr(), FakePtr(), 0) \

@@ -71,6 +71,19 @@ def test_coop_rejects_bad_splits():
     small = torch.zeros(16, dtype=torch.uint8, device="cuda")
     with pytest.raises(hea.HeaError):
         hea.hea_search_coop(lat, obj, hea.search_params(64, 1), 2, buf, buf, res, small)
+    # more merged records than the walk holds (ctas * group_top > 640)
+    with pytest.raises(hea.HeaError) as e:
+        hea.hea_search_coop(lat, obj, hea.search_params(200 * 4, 1, accept_mode=1, group_size=4, group_top=4), 200,
+                            buf, buf, res, torch.zeros(hea.hea_search_coop_workspace_bytes(200), dtype=torch.uint8,
+                                                       device="cuda"))
+    assert e.value.status == hea.HEA_EINVAL and "640" in str(e.value)
+    # the withholding test aid belongs to cooperative searches only, and must name one of the CTAs
+    with pytest.raises(hea.HeaError) as e:
+        hea.hea_search(lat, obj, hea.search_params(64, 1, test_withhold_cta=1), buf, buf, res)
+    assert e.value.status == hea.HEA_EINVAL
+    with pytest.raises(hea.HeaError) as e:
+        hea.hea_search_coop(lat, obj, hea.search_params(64, 1, test_withhold_cta=3), 2, buf, buf, res, buf)
+    assert e.value.status == hea.HEA_EINVAL
 
 
 def test_coop_time_budget():
@@ -100,3 +113,111 @@ def test_coop_fcc_256k_all_sms_prefix(top):
                       ctas, **kw)
     assert_same(g, o)
     assert g[2]["accepted"] > 6
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_coop_wait_for_a_withheld_cta_runs_out(mode):
+    """One CTA never publishes its records: every other CTA's wait for them is bounded (here 20 ms),
+    the search ends with HEA_ESYNC after no completed step, the state written back is the input state,
+    and the GPU context stays usable (the next search on the same workspace is bit-exact)."""
+    import time
+    import torch
+    kind, L, M, S = FCC, (8, 8, 8), 3, 4
+    N = oracle.num_sites(kind, L)
+    n_per = workloads.equiatomic(N, S)
+    w, target = np.ones(M), np.zeros((M, S, S))
+    t = oracle.init_config(N, n_per, 3)
+    cnt = oracle.counts(kind, L, M, S, t)
+    ctas = min(8, G.sm_count())
+    kw = dict(K=ctas * 64, max_steps=50, accept_mode=mode, seed=7)
+    if mode == 1:
+        kw.update(group_size=64, group_top=2)
+    G.ensure_built()
+    lat = hea.Lattice(kind, L, M)
+    obj = hea.Objective(n_per, w, target)
+    ws = torch.zeros(hea.hea_search_coop_workspace_bytes(ctas), dtype=torch.uint8, device="cuda")
+    tg, cg = G.dev(t), G.dev(cnt)
+    res = torch.zeros(hea.RESULT_BYTES, dtype=torch.uint8, device="cuda")
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    hea.hea_search_coop(lat, obj, hea.search_params(**kw, sync_wait_us=20000, test_withhold_cta=4), ctas, tg, cg,
+                        res, ws)
+    torch.cuda.synchronize()
+    elapsed = time.perf_counter() - t0
+    r = hea.decode_results(res.cpu().numpy())[0]
+    assert r["status"] == hea.HEA_ESYNC and r["steps"] == 0 and r["accepted"] == 0
+    assert elapsed < 1.5
+    assert np.array_equal(tg.cpu().numpy(), t) and np.array_equal(cg.cpu().numpy(), cnt)
+    # the same workspace, no CTA withheld: identical to the oracle
+    hea.hea_search_coop(lat, obj, hea.search_params(**kw), ctas, tg, cg, res, ws)
+    torch.cuda.synchronize()
+    o = oracle.search(kind, L, M, n_per, w, target, t, cnt, **kw)[:3]
+    assert_same((tg.cpu().numpy(), cg.cpu().numpy(), hea.decode_results(res.cpu().numpy())[0]), o)
+
+
+def test_coop_fcc_256k_bench_trajectory_checkpoints():
+    """The benchmark's launch (FCC 40^3, annealed target, one CTA per SM, bench.py's candidates and
+    published records per CTA, seed 1) over its whole trajectory: from checkpoints at steps 100 and
+    300, just before the last step that accepts a swap (where keys are tiny and intervals matter
+    most) and 3 steps before the end, 3 GPU steps and 3 oracle steps (resumed with step0 / depth0)
+    agree bit for bit; the full run ends in a state whose counts are its recount."""
+    from bench import COOP_KC, COOP_TOP, TRIALS_PER_STEP
+    spec = workloads.fcc_256k()
+    ctas = G.sm_count()
+    K = ctas * COOP_KC
+    total = TRIALS_PER_STEP // K
+    base = dict(K=K, accept_mode=1, group_size=COOP_KC, group_top=COOP_TOP, seed=spec.seed)
+    args = (spec.kind, spec.L, spec.M, spec.n_per, spec.weights(), spec.targets())
+    t0 = oracle.init_config(spec.N, spec.n_per, spec.seed)
+    c0 = oracle.counts(spec.kind, spec.L, spec.M, spec.S, t0)
+    tf, cf, rf = G.gpu_search_coop(*args, t0, c0, ctas, max_steps=total, **base)
+    assert rf["status"] == 0 and rf["steps"] == total and rf["accepted"] > 0
+    assert np.array_equal(cf, oracle.counts(spec.kind, spec.L, spec.M, spec.S, tf))
+    _, f2 = oracle.alpha_f2(spec.kind, spec.L, spec.M, spec.n_per, spec.weights(), spec.targets(), cf)
+    assert rf["f2"] == f2
+    last = total - rf["depth"] - 1          # last step that accepted a swap
+    for s in sorted({100, 300, max(1, last - 1), total - 3}):
+        ts, cs, rs = G.gpu_search_coop(*args, t0, c0, ctas, max_steps=s, **base)
+        kw = dict(base, max_steps=3, step0=s, depth0=rs["depth"])
+        g = G.gpu_search_coop(*args, ts, cs, ctas, **kw)
+        o = oracle.search(*args, ts, cs, **kw)[:3]
+        assert_same(g, o)
+        if s == total - 3:
+            assert np.array_equal(g[0], tf) and np.array_equal(g[1], cf)
+
+
+@pytest.mark.parametrize("mode,top", [(0, 1), (1, 1), (1, 3)])
+def test_coop_massive_key_ties_from_ordered_start(mode, top):
+    """B2-ordered BCC 8^3 with a zero target on 8 CTAs: swaps with identical surroundings have
+    bit-identical keys in different CTAs, so the fixed-point intervals of the published records
+    overlap and their order falls back to binary64 keys and k; bit-exact against the oracle."""
+    kind, L, M, S = BCC, (8, 8, 8), 3, 2
+    pos = oracle.positions(kind, L)
+    t = (pos[:, 0] % 2).astype(np.uint8)
+    n_per = [512, 512]
+    cnt = oracle.counts(kind, L, M, S, t)
+    w, target = np.ones(M), np.zeros((M, S, S))
+    ctas, Kc = 8, 64
+    kw = dict(K=ctas * Kc, max_steps=6, accept_mode=mode, seed=3)
+    if mode == 1:
+        kw.update(group_size=Kc, group_top=top)
+    g = G.gpu_search_coop(kind, L, M, n_per, w, target, t, cnt, ctas, **kw)
+    o = oracle.search(kind, L, M, n_per, w, target, t, cnt, **kw)[:3]
+    assert_same(g, o)
+    assert o[2]["accepted"] > 0
+
+
+@pytest.mark.parametrize("Kc,top", [(2500, 1), (1500, 3)])
+def test_coop_slices_scored_in_chunks(Kc, top):
+    """A CTA's slice larger than one scoring pass (1024 candidates) is scored in chunks with the best
+    candidates so far carried between them: bit-exact against the oracle's group rule."""
+    kind, L, M, S = FCC, (8, 8, 8), 3, 4
+    N = oracle.num_sites(kind, L)
+    rng = np.random.default_rng(Kc)
+    n_per = composition(N, S, rng)
+    w, target = random_objective(M, S, rng, scale=0.8, symmetric=True)
+    ctas = 8
+    kw = dict(K=ctas * Kc, max_steps=8, accept_mode=1, group_size=Kc, group_top=top, seed=13)
+    g, o, _, _ = both(kind, L, M, S, n_per, w, target, 6, ctas, **kw)
+    assert_same(g, o)
+    assert o[2]["accepted"] > 0

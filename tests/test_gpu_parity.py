@@ -359,3 +359,17 @@ def test_search_massive_key_ties_from_ordered_start(mode, K):
     to, co, ro, _ = oracle.search(kind, L, M, n_per, w, target, t, cnt, K=K, max_steps=6, accept_mode=mode, seed=3)
     assert_same((tg, cg, rg), (to, co, ro))
     assert ro["accepted"] > 0
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_two_bit_species_storage_half_million_sites(mode):
+    """FCC 50^3 (500,000 sites, 4 species): the cell fits one CTA's shared memory only at 2 bits per
+    site; a prefix of the trajectory bit-exact against the oracle."""
+    kind, L, M, S = FCC, (50, 50, 50), 3, 4
+    N = oracle.num_sites(kind, L)
+    entry = workloads.annealed_targets()["pool_fcc_4sp"][2]
+    n_per = workloads.composition_counts(N, entry["fractions"])
+    g, o = run_both(kind, L, M, S, n_per, np.ones(M), np.array(entry["alpha"]), 5, K=256, max_steps=8,
+                    accept_mode=mode, seed=4)
+    assert_same(g, o)
+    assert o[2]["accepted"] > 0
