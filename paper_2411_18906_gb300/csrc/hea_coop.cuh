@@ -44,7 +44,7 @@ namespace hea {
 
 constexpr int kFixBitsA = 32;   // |A_e| < 2^32
 constexpr int kFixBitsB = 38;   // |B_e| < 2^38 at the step start
-constexpr int kFixBitsW = 36;   // walk: bound on the running |b| below 2^36 (2^38 with the bound's margin)
+constexpr int kFastEdges = 64;  // the walk's fast path handles at most this many conflicting record pairs
 
 // Largest F with maxabs 2^F < 2^bits (maxabs finite, >= 0); a large value when maxabs is 0.
 __device__ __forceinline__ int fix_scale(double maxabs, int bits) {
@@ -198,7 +198,7 @@ __device__ __forceinline__ void slot_fixed(ChainSmem& m, const ChainCtx& c, int 
     fix_key(c.M, c.S, m.fA, m.fB, nullptr, A, B, m.qg + q * c.M, shA, fix, eps);
     m.qfix[q] = fix;
     m.qeps[q] = eps;
-    m.qflag[q] |= 16u;
+    atomicOr(&m.qflag[q], 16u);   // several threads may settle the same slot (same values)
 }
 
 template <int BITS>
@@ -206,7 +206,7 @@ __device__ __forceinline__ void slot_exact(ChainSmem& m, const ChainCtx& c, int 
     if (m.qflag[q] & 1u) return;
     const int A = load_species<BITS>(m.types, m.qa[q]), B = load_species<BITS>(m.types, m.qb[q]);
     m.qD[q] = exact_key(c.M, c.S, m.ca, m.cb, A, B, m.qg + q * c.M);
-    m.qflag[q] |= 1u;
+    atomicOr(&m.qflag[q], 1u);
 }
 
 // 1 when slot p's key comes first in (D, k) order, 0 when q's does, -1 when the precision both
@@ -445,6 +445,53 @@ static __device__ bool coop_gather(const ChainDesc& d, ChainSmem& m, ChainShared
     return true;
 }
 
+// ---- rank of a list of slots among themselves by (D, k) ------------------------------------------
+// rank(list[x]) = number of list members before it, taken on FP32 intervals, then (for the pairs
+// the intervals leave open) on fixed-point keys, then binary64 keys.  Writes m.acc[slot] = rank and
+// sorted[rank] = slot.
+template <int BITS>
+__device__ void rank_list(ChainSmem& m, ChainShared& sh, const ChainCtx& c, const uint16_t* list, int n,
+                          uint16_t* sorted) {
+    const int tid = threadIdx.x, T = blockDim.x;
+    const int shA = sh.fixFa - sh.fixF;
+    for (int tier = 0; tier < 3; ++tier) {
+        if (tid == 0) sh.n_amb = 0;
+        __syncthreads();
+        for (int x = tid; x < n; x += T) {
+            const int q = list[x];
+            uint32_t cnt = 0u;
+            bool open = false;
+            for (int y = 0; y < n; ++y) {
+                const int p = list[y];
+                if (p == q) continue;
+                const int o = slot_order<BITS>(m, c, p, q);
+                if (o < 0)
+                    open = true;
+                else
+                    cnt += (uint32_t)o;
+            }
+            m.acc[q] = cnt;
+            if (open) {
+                m.qflag[q] |= 8u;
+                sh.n_amb = 1;
+            }
+        }
+        __syncthreads();
+        if (!sh.n_amb) break;
+        for (int x = tid; x < n; x += T) {
+            const int q = list[x];
+            if (m.qflag[q] & 8u) {
+                if (tier == 0) slot_fixed<BITS>(m, c, q, shA);
+                else slot_exact<BITS>(m, c, q);
+                m.qflag[q] &= ~8u;
+            }
+        }
+        __syncthreads();
+    }
+    for (int x = tid; x < n; x += T) sorted[m.acc[list[x]]] = list[x];
+    __syncthreads();
+}
+
 // ---- 5a. global rank of the merged records by (D, k) --------------------------------------------
 // rank(q) = number of records before q.  First counted on the FP32 intervals; records whose interval
 // overlaps another's are flagged and, for them only, the open pairs are settled with fixed-point
@@ -525,7 +572,11 @@ struct CoopWalk {
     uint32_t* site;    // [nrec][2]
     uint8_t* spec;     // [nrec][2] species of a and b at the step start
     int16_t* pos;      // [nrec][6] half-unit positions of a and b
-    uint32_t* conf;    // [nrec][nw] bit i of row r: candidates i < r conflict
+    // (dense, site, spec, pos and conf are indexed by slot; the walk reaches them through m.order)
+    uint32_t* conf;    // [nrec][nw] bit q' of row q: merged records q and q' conflict (slot space)
+    int32_t* Ptot;     // [Ep] sum over the records of |dN_e|
+    uint32_t* accb;    // [2 nw] fast path: accepted records, then scratch (slot space)
+    uint32_t* edge;    // [2 nrec] conflicting record pairs (slot << 16 | slot)
     uint32_t* cellA;   // occupancy of hashed conventional cells (one bit per hash value)
     uint32_t* cellB;   // cells occupied more than once
     uint16_t* susp;    // sites (2 r + 0 / 1) near another candidate's site
@@ -556,6 +607,12 @@ __device__ __forceinline__ CoopWalk coop_walk_arrays(uint8_t* p, int nrec, int E
     p += align_up(12 * n, 16);
     w.conf = reinterpret_cast<uint32_t*>(p);
     p += align_up(4 * n * nw, 16);
+    w.Ptot = reinterpret_cast<int32_t*>(p);
+    p += align_up(4 * Ep, 16);
+    w.accb = reinterpret_cast<uint32_t*>(p);
+    p += align_up(8 * nw, 16);
+    w.edge = reinterpret_cast<uint32_t*>(p);
+    p += align_up(8 * n, 16);
     w.cellA = reinterpret_cast<uint32_t*>(p);
     p += kCoopCellWords * 4;
     w.cellB = reinterpret_cast<uint32_t*>(p);
@@ -590,7 +647,7 @@ __device__ __forceinline__ void batch_rows(const CoopWalk& w, const ChainSmem& m
                                            int Ws) {
     for (int x = threadIdx.x; x < nb * Ep; x += blockDim.x) {
         const int j = x / Ep, e = x - j * Ep;
-        const float v = (float)w.dense[(r0 + j) * Ep + e];
+        const float v = (float)w.dense[m.order[r0 + j] * Ep + e];
         w.R[j * Ws + e] = v;
         w.W[j * Ws + e] = (e < E) ? m.fa[e] * v : 0.0f;
     }
@@ -599,6 +656,7 @@ __device__ __forceinline__ void batch_rows(const CoopWalk& w, const ChainSmem& m
 // Hash of a conventional cell (cx, cy, cz) into the occupancy bitmaps.
 __device__ __forceinline__ uint32_t cell_hash(const Geo& g, int cx, int cy, int cz) {
     const uint32_t cell = ((uint32_t)cz * (uint32_t)g.Ly + (uint32_t)cy) * (uint32_t)g.Lx + (uint32_t)cx;
+    if ((uint32_t)g.V <= (1u << kCoopCellBits)) return cell;   // one bit per cell
     return (cell * 0x9E3779B1u) >> (32 - kCoopCellBits);
 }
 
@@ -612,21 +670,21 @@ __device__ void coop_walk(const ChainDesc& d, ChainSmem& m, ChainShared& sh, con
     CoopWalk w = coop_walk_arrays(m.walk, d.nrec, E);
     const int reach = c_shells[KIND].reach[M - 1];
     const int rc = (reach + 1) / 2;   // sites within shell M lie in cells at most rc apart per axis
-    // P0: sites, step-start species, positions of the ranked candidates; cell occupancy.
-    for (int r = tid; r < ne; r += T) {
-        const uint32_t q = m.order[r];
+    // P0: sites, step-start species and positions of the merged records (slot space); occupancy of
+    // their conventional cells.
+    for (int q = tid; q < ne; q += T) {
         const uint32_t a = m.qa[q], b = m.qb[q];
-        w.site[2 * r] = a;
-        w.site[2 * r + 1] = b;
-        w.spec[2 * r] = (uint8_t)load_species<BITS>(m.types, a);
-        w.spec[2 * r + 1] = (uint8_t)load_species<BITS>(m.types, b);
+        w.site[2 * q] = a;
+        w.site[2 * q + 1] = b;
+        w.spec[2 * q] = (uint8_t)load_species<BITS>(m.types, a);
+        w.spec[2 * q + 1] = (uint8_t)load_species<BITS>(m.types, b);
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
             int X, Y, Z;
             site_coords<KIND>(c.g, h ? b : a, X, Y, Z);
-            w.pos[6 * r + 3 * h + 0] = (int16_t)X;
-            w.pos[6 * r + 3 * h + 1] = (int16_t)Y;
-            w.pos[6 * r + 3 * h + 2] = (int16_t)Z;
+            w.pos[6 * q + 3 * h + 0] = (int16_t)X;
+            w.pos[6 * q + 3 * h + 1] = (int16_t)Y;
+            w.pos[6 * q + 3 * h + 2] = (int16_t)Z;
             const uint32_t hc = cell_hash(c.g, X >> 1, Y >> 1, Z >> 1);
             const uint32_t bit = 1u << (hc & 31);
             if (atomicOr(&w.cellA[hc >> 5], bit) & bit) atomicOr(&w.cellB[hc >> 5], bit);
@@ -634,23 +692,32 @@ __device__ void coop_walk(const ChainDesc& d, ChainSmem& m, ChainShared& sh, con
     }
     for (int x = tid; x < ne * nw; x += T) w.conf[x] = 0u;
     for (int x = tid; x < nw; x += T) sh.taken[x] = 0u;
+    for (int e = tid; e < Ep; e += T) w.Ptot[e] = 0;
     if (tid == 0) {
         sh.n_acc = 0;
         sh.walk_done = 0;
         sh.n_pairs = 0;
+        sh.n_amb = 0;
+        sh.n_edges = 0;
     }
     __syncthreads();
-    // P1: dense count changes, one (candidate, shell) block each; suspects: sites whose own cell
-    // holds another candidate site or whose neighbouring cells hold any.
+    // P1: dense count changes, one (record, shell) block each, and their per-entry totals; suspects:
+    // sites whose own cell holds another record's site or whose neighbouring cells hold any.
     for (int x = tid; x < ne * M; x += T) {
-        const int r = x / M, k = x - r * M;
-        const int A = w.spec[2 * r], B = w.spec[2 * r + 1];
-        const uint64_t g_k = m.qg[m.order[r] * M + k];
-        int8_t* row = w.dense + r * Ep + k * SS;
-        for (int i = 0; i < S; ++i)
-            for (int j = 0; j < S; ++j) row[i * S + j] = (int8_t)entry_delta(g_k, A, B, i, j);
+        const int q = x / M, k = x - q * M;
+        const int A = w.spec[2 * q], B = w.spec[2 * q + 1];
+        const uint64_t g_k = m.qg[q * M + k];
+        int8_t* row = w.dense + q * Ep + k * SS;
+        // entries visited from a lane-dependent start, so that the lanes' atomics on the per-entry
+        // totals rarely meet on one address
+        for (int t = 0, idx = lane % SS; t < SS; ++t, idx = (idx + 1 == SS) ? 0 : idx + 1) {
+            const int i = idx / S, j = idx - i * S;
+            const int v = entry_delta(g_k, A, B, i, j);
+            row[idx] = (int8_t)v;
+            if (v) atomicAdd(&w.Ptot[k * SS + idx], v < 0 ? -v : v);
+        }
         if (k == M - 1)
-            for (int e = E; e < Ep; ++e) w.dense[r * Ep + e] = 0;
+            for (int e = E; e < Ep; ++e) w.dense[q * Ep + e] = 0;
     }
     for (int s2 = tid; s2 < 2 * ne; s2 += T) {
         const int16_t* P3 = w.pos + 3 * s2;
@@ -672,7 +739,11 @@ __device__ void coop_walk(const ChainDesc& d, ChainSmem& m, ChainShared& sh, con
     __syncthreads();
     // P2: exact conflicts among the suspects (minimum-image distance within shell M, the same relation
     // as closed shell neighbourhoods for cells of at least two conventional cells per axis); the
-    // occupancy bits are cleared for the next step.
+    // occupancy bits are cleared for the next step.  Sure records: accepting any set of the other
+    // records shifts a record's key by 2 sum_i X(i, j), |.| <= U = 2 sum_e |a_e| |dN_j,e| sum_i |dN_i,e|;
+    // a record whose step-start interval stays eligible under that shift (plus the roundings of the
+    // binary64 coefficients at the running counts) is accepted unless a conflicting record before it
+    // is.
     {
         const int ns = sh.n_pairs;
         const int r2max = c_shells[KIND].radius2[M - 1];
@@ -680,16 +751,20 @@ __device__ void coop_walk(const ChainDesc& d, ChainSmem& m, ChainShared& sh, con
         for (int x = tid; x < ns * ns; x += T) {
             const int u = x / ns, v = x - u * ns;
             if (u >= v) continue;
-            const int s = w.susp[u], t = w.susp[v];
-            const int rs = s >> 1, rt = t >> 1;
-            if (rs == rt) continue;
-            const int16_t* P = w.pos + 3 * s;
-            const int16_t* Q = w.pos + 3 * t;
+            const int s0 = w.susp[u], t0 = w.susp[v];
+            const int qs = s0 >> 1, qt = t0 >> 1;
+            if (qs == qt) continue;
+            const int16_t* P = w.pos + 3 * s0;
+            const int16_t* Q = w.pos + 3 * t0;
             const int dx = wrap_min_image(P[0] - Q[0], PX), dy = wrap_min_image(P[1] - Q[1], PY),
                       dz = wrap_min_image(P[2] - Q[2], PZ);
             if (dx * dx + dy * dy + dz * dz <= r2max) {
-                const int lo = min(rs, rt), hi = max(rs, rt);
-                atomicOr(&w.conf[hi * nw + (lo >> 5)], 1u << (lo & 31));
+                const uint32_t old_bit = atomicOr(&w.conf[qs * nw + (qt >> 5)], 1u << (qt & 31));
+                atomicOr(&w.conf[qt * nw + (qs >> 5)], 1u << (qs & 31));
+                if (!((old_bit >> (qt & 31)) & 1u)) {   // a new edge (several site pairs may find it)
+                    const int x = atomicAdd(&sh.n_edges, 1);
+                    if (x < 2 * d.nrec) w.edge[x] = ((uint32_t)qs << 16) | (uint32_t)qt;
+                }
             }
         }
         for (int s2 = tid; s2 < 2 * ne; s2 += T) {
@@ -698,8 +773,103 @@ __device__ void coop_walk(const ChainDesc& d, ChainSmem& m, ChainShared& sh, con
             atomicAnd(&w.cellA[hc >> 5], ~(1u << (hc & 31)));
             atomicAnd(&w.cellB[hc >> 5], ~(1u << (hc & 31)));
         }
-        batch_rows(w, m, 0, min(32, ne), E, Ep, Ws);
+        for (int q = tid; q < ne; q += T) {
+            const int8_t* row = w.dense + q * Ep;
+            float U = 0.f, tin = 0.f;
+            for (int e = 0; e < E; ++e) {
+                const int dl = row[e];
+                if (dl == 0) continue;
+                const float ad = (float)(dl < 0 ? -dl : dl);
+                U = fmaf(fabsf(m.fa[e]) * ad, (float)w.Ptot[e], U);
+                tin = fmaf(ad, 2.0f * m.tiny[e], tin);
+            }
+            U = 2.0f * U * (1.0f + 16.0f * kTwoUlp);
+            const float hi = m.qhi[q], lo = m.qlo[q];
+            const float slack = fmaf(kTwoPow20, (hi - lo) + U, tin + kAbsBound);
+            const float top = __fadd_ru(__fadd_ru(hi, U), slack);
+            const bool sure = c.pos_thr ? (top <= c.thr_lo) : (top < 0.f);
+            if (sure)
+                m.qflag[q] |= 64u;
+            else
+                sh.n_amb = 1;
+        }
     }
+    __syncthreads();
+    if (!sh.n_amb && d.max_accept == 0 && sh.n_edges <= kFastEdges) {
+        // Fast path: every record is accepted unless it conflicts with an accepted record before it
+        // in (D, k) order.  Only the conflicting pairs need an order: one thread per edge orients it
+        // (at the precision that settles it), then the greedy choice is the fixed point of
+        // "accepted unless an accepted neighbour comes first", reached from all-accepted in at most
+        // (longest chain of edges + 1) sweeps.
+        const int ned = sh.n_edges;
+        const int shA = sh.fixFa - sh.fixF;
+        for (int x = tid; x < nw; x += T) w.accb[x] = (x == nw - 1 && (ne & 31)) ? ((1u << (ne & 31)) - 1u) : 0xFFFFFFFFu;
+        for (int x = tid; x < ned; x += T) {
+            const int u = (int)(w.edge[x] >> 16), v = (int)(w.edge[x] & 0xFFFFu);
+            int o = slot_order<BITS>(m, c, u, v);
+            if (o < 0) {
+                slot_fixed<BITS>(m, c, u, shA);
+                slot_fixed<BITS>(m, c, v, shA);
+                o = slot_order<BITS>(m, c, u, v);
+            }
+            if (o < 0) {
+                slot_exact<BITS>(m, c, u);
+                slot_exact<BITS>(m, c, v);
+                o = slot_order<BITS>(m, c, u, v);
+            }
+            // stored as (first << 16) | second
+            w.edge[x] = o == 1 ? (((uint32_t)u << 16) | (uint32_t)v) : (((uint32_t)v << 16) | (uint32_t)u);
+        }
+        __syncthreads();
+        if (tid == 0) {
+            uint32_t* pred = w.accb + nw;   // records with an accepted record before them in a conflict
+            for (int sweep = 0; sweep <= ned; ++sweep) {
+                for (int y = 0; y < nw; ++y) pred[y] = 0u;
+                for (int x = 0; x < ned; ++x) {
+                    const int u = (int)(w.edge[x] >> 16), v = (int)(w.edge[x] & 0xFFFFu);
+                    if ((w.accb[u >> 5] >> (u & 31)) & 1u) pred[v >> 5] |= 1u << (v & 31);
+                }
+                bool changed = false;
+                for (int x = 0; x < ned; ++x) {
+                    const int v = (int)(w.edge[x] & 0xFFFFu);
+                    const uint32_t bit = 1u << (v & 31);
+                    const bool want = !(pred[v >> 5] & bit), acc = (w.accb[v >> 5] & bit) != 0u;
+                    if (want != acc) {
+                        w.accb[v >> 5] ^= bit;
+                        changed = true;
+                    }
+                }
+                if (!changed) break;
+            }
+        }
+        __syncthreads();
+        // apply every accepted swap: counts, species
+        {
+            const int parts = max(1, T / max(E, 1));
+            for (int x = tid; x < E * parts; x += T) {
+                const int e = x % E, part = x / E;
+                int dl = 0;
+                for (int q = part; q < ne; q += parts)
+                    if ((w.accb[q >> 5] >> (q & 31)) & 1u) dl += w.dense[q * Ep + e];
+                if (dl) atomicAdd(&m.cnt[e], dl);
+            }
+            for (int q = tid; q < ne; q += T)
+                if ((w.accb[q >> 5] >> (q & 31)) & 1u) {
+                    store_species_atomic<BITS>(m.types, w.site[2 * q], w.spec[2 * q + 1]);
+                    store_species_atomic<BITS>(m.types, w.site[2 * q + 1], w.spec[2 * q]);
+                    atomicAdd(&sh.n_acc, 1);
+                }
+        }
+        __syncthreads();
+        return;
+    }
+    // Full path: rank the records by (D, k) (m.order: rank -> slot, m.acc: slot -> rank), then walk.
+    coop_rank<BITS>(m, sh, c, ne);
+    if (tid == 0) sh.n_pairs = 0;   // bit b: batch b holds a candidate that is not sure
+    __syncthreads();
+    batch_rows(w, m, 0, min(32, ne), E, Ep, Ws);
+    for (int r = tid; r < ne; r += T)
+        if (!(m.qflag[m.order[r]] & 64u)) atomicOr(reinterpret_cast<unsigned int*>(&sh.n_pairs), 1u << (r >> 5));
     __syncthreads();
     // The walk in batches of 32 ranked candidates.  For each batch, in parallel: its rows, its
     // candidates' keys against the running state at the start of the batch (FP32 estimates of the
@@ -712,9 +882,11 @@ __device__ void coop_walk(const ChainDesc& d, ChainSmem& m, ChainShared& sh, con
         if (sh.walk_done) break;
         const int nb = min(32, ne - r0);
         const int acc_before = sh.n_acc;
+        const bool batch_sure = !((sh.n_pairs >> (r0 >> 5)) & 1);
         // W1: running keys (16 threads per candidate) and cross terms (one warp per column) of the batch,
-        // whose rows were built in the previous phase.
+        // whose rows were built in the previous phase; not needed when every candidate is sure.
         // warp-uniform loop: every lane of a warp takes part in the shuffles
+        if (!batch_sure) {
         for (int x0 = tid - lane; x0 < 16 * nb; x0 += T) {
             const int x = x0 + lane;
             const bool act = x < 16 * nb;
@@ -788,6 +960,7 @@ __device__ void coop_walk(const ChainDesc& d, ChainSmem& m, ChainShared& sh, con
             }
         }
         __syncthreads();
+        }
         // W2: decisions, in order, by warp 0; lane j holds candidate j of the batch.  Speculation:
         // every undecided lane evaluates its candidate assuming that all earlier undecided candidates
         // not blocked by earlier batches are accepted; the first lane whose decision contradicts that
@@ -799,18 +972,28 @@ __device__ void coop_walk(const ChainDesc& d, ChainSmem& m, ChainShared& sh, con
             uint32_t prior = 1u, mask = 0u;
             const float *PXl = w.PX + lane * 33, *PEl = w.PE + lane * 33, *PAl = w.PA + lane * 33;
             const float* XTl = w.XT + lane * 33;
+            bool sure = true;
             if (lane < nb) {
-                const int r = r0 + lane;
-                D0 = w.bD[lane];
-                E0 = w.bE[lane];
+                const int q = m.order[r0 + lane];
+                sure = (m.qflag[q] & 64u) != 0u;
+                if (!batch_sure) {
+                    D0 = w.bD[lane];
+                    E0 = w.bE[lane];
+                    pxj = PXl[lane];
+                    pej = PEl[lane];
+                    paj = PAl[lane];
+                }
                 // conflicts with the swaps accepted in earlier batches, and with earlier candidates here
-                uint32_t pr = 0u;
-                for (int x = 0; x < (r0 >> 5); ++x) pr |= w.conf[r * nw + x] & sh.taken[x];
-                prior = pr != 0u ? 1u : 0u;
-                mask = w.conf[r * nw + (r0 >> 5)] & ((1u << lane) - 1u);
-                pxj = PXl[lane];
-                pej = PEl[lane];
-                paj = PAl[lane];
+                prior = 0u;
+                for (int y = 0; y < nw; ++y)
+                    for (uint32_t bits = w.conf[q * nw + y]; bits; bits &= bits - 1u) {
+                        const int rq = (int)m.acc[32 * y + __ffs(bits) - 1];   // rank of the other record
+                        if (rq < r0) {
+                            if ((sh.taken[rq >> 5] >> (rq & 31)) & 1u) prior = 1u;
+                        } else if (rq < r0 + lane) {
+                            mask |= 1u << (rq - r0);
+                        }
+                    }
             }
             const uint32_t open = __ballot_sync(0xFFFFFFFFu, lane < nb && prior == 0u);
             // candidates blocked by earlier batches are never accepted: their cross terms, included in
@@ -827,8 +1010,8 @@ __device__ void coop_walk(const ChainDesc& d, ChainSmem& m, ChainShared& sh, con
                     const uint32_t gl = guess & ((1u << lane) - 1u);
                     const bool blocked = prior != 0u || (mask & (accm | gl)) != 0u;
                     if (!blocked) {
-                        if (acc_before == 0 && (accm | gl) == 0u) {
-                            dec = 1;   // the step-start state: the candidate is eligible
+                        if (sure || (acc_before == 0 && (accm | gl) == 0u)) {
+                            dec = 1;   // sure, or the step-start state: the candidate is eligible
                         } else {
                             float sx = cc + (pxj - PXl[p]);
                             for (uint32_t bb = blk & gl_span(p, lane); bb; bb &= bb - 1u) sx -= XTl[__ffs(bb) - 1];
@@ -874,11 +1057,14 @@ __device__ void coop_walk(const ChainDesc& d, ChainSmem& m, ChainShared& sh, con
                 int dj = __shfl_sync(0xFFFFFFFFu, dec, js);
                 if (dj < 0) {
                     // The bound leaves it open: the reference key against the running counts.
-                    const int r = r0 + js;
+                    const int qj = m.order[r0 + js];
                     double Dp = 0.0;
-                    if (lane == 0)
-                        Dp = exact_key_pending(M, S, m.cnt, m.Q, m.tgt, m.ca, d.w, w.spec[2 * r], w.spec[2 * r + 1],
-                                               m.qg + m.order[r] * M, w.dense + r0 * Ep, Ep, sh.red_q, nbacc);
+                    if (lane == 0) {
+                        int pend[32];
+                        for (int x = 0; x < nbacc; ++x) pend[x] = (int)m.order[r0 + sh.red_q[x]];
+                        Dp = exact_key_pending(M, S, m.cnt, m.Q, m.tgt, m.ca, d.w, w.spec[2 * qj], w.spec[2 * qj + 1],
+                                               m.qg + qj * M, w.dense, Ep, pend, nbacc);
+                    }
                     Dp = __shfl_sync(0xFFFFFFFFu, Dp, 0);
                     dj = eligible(Dp, false, c.thr) ? 1 : 0;
                 }
@@ -909,7 +1095,7 @@ __device__ void coop_walk(const ChainDesc& d, ChainSmem& m, ChainShared& sh, con
         if (nba > 0) {
             for (int e = tid; e < E; e += T) {
                 int dl = 0;
-                for (int x = 0; x < nba; ++x) dl += w.dense[(r0 + sh.red_q[x]) * Ep + e];
+                for (int x = 0; x < nba; ++x) dl += w.dense[m.order[r0 + sh.red_q[x]] * Ep + e];
                 if (dl == 0) continue;
                 m.cnt[e] += dl;
                 const int dn = m.dn[e] + dl;
@@ -917,9 +1103,9 @@ __device__ void coop_walk(const ChainDesc& d, ChainSmem& m, ChainShared& sh, con
                 running_coefficient(e, dn, m.fw[e], m.fQ, m.fe0, m.tiny, m.fb, m.beta);
             }
             for (int x = tid; x < nba; x += T) {
-                const int r = r0 + sh.red_q[x];
-                store_species_atomic<BITS>(m.types, w.site[2 * r], w.spec[2 * r + 1]);
-                store_species_atomic<BITS>(m.types, w.site[2 * r + 1], w.spec[2 * r]);
+                const int r = r0 + sh.red_q[x], q = m.order[r];
+                store_species_atomic<BITS>(m.types, w.site[2 * q], w.spec[2 * q + 1]);
+                store_species_atomic<BITS>(m.types, w.site[2 * q + 1], w.spec[2 * q]);
                 atomicOr(&sh.taken[r >> 5], 1u << (r & 31));
             }
         }
@@ -1058,7 +1244,6 @@ __device__ void run_coop_chain(const ChainDesc& d, uint8_t* smem, ChainShared& s
             }
         } else {
             const int ne = sh.qn;
-            coop_rank<BITS>(m, sh, c, ne);
             coop_walk<KIND, BITS>(d, m, sh, c, ne);
             coop_after_walk(d, m, sh, c);
         }

@@ -133,12 +133,13 @@ __host__ __device__ inline ChainLayout chain_layout(int N, int M, int S, int qca
 // Data of the multi-accept walk of a cooperative chain over at most `nrec` ranked candidates (E
 // entries, rows of Ep = E rounded up to 4): dense count changes int8 [nrec][Ep], sites u32
 // [nrec][2], species u8 [nrec][2], positions int16 [nrec][6], the conflict matrix u32
-// [nrec][ceil(nrec / 32)], two occupancy bitmaps of hashed conventional cells (kCoopCellBits bits
+// [nrec][ceil(nrec / 32)], per-entry totals int32 [Ep], accepted-record and scratch masks u32
+// [2][ceil(nrec / 32)], conflicting pairs u32 [2 nrec], two occupancy bitmaps of hashed conventional cells (kCoopCellBits bits
 // each), suspect sites u16 [2 nrec], then one batch of 32: rows float [32][Ws] x 2 (Ws: Ep padded
 // to 4 mod 8), cross terms, their bounds and three prefix-sum tables float [32][33] x 5, keys and
 // bounds float [32] x 2, conflict masks u32 [32] x 2.  The device-side pointers (coop_walk_arrays)
 // follow this order.
-constexpr int kCoopCellBits = 15;
+constexpr int kCoopCellBits = 16;
 constexpr uint32_t kCoopCellWords = (1u << kCoopCellBits) / 32u;
 
 __host__ __device__ inline uint32_t coop_walk_bytes(int nrec, int E) {
@@ -146,7 +147,9 @@ __host__ __device__ inline uint32_t coop_walk_bytes(int nrec, int E) {
     const uint32_t Ws = (Ep % 8u == 4u) ? Ep : Ep + 4u;   // batch row stride (floats)
     const uint32_t nw = (n + 31u) / 32u;
     return align_up(n * Ep, 16) + align_up(8 * n, 16) + align_up(2 * n, 16) + align_up(12 * n, 16) +
-           align_up(4 * n * nw, 16) + 2 * 4 * kCoopCellWords + align_up(4 * n, 16) + 2 * 4 * 32 * Ws +
+           align_up(4 * n * nw, 16) + align_up(4 * Ep, 16) + align_up(8 * nw, 16) + align_up(8 * n, 16) +
+           2 * 4 * kCoopCellWords +
+           align_up(4 * n, 16) + 2 * 4 * 32 * Ws +
            5 * 4 * 32 * 33 + 2 * 4 * 32 + 2 * 4 * 32;
 }
 

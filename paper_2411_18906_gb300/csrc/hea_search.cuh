@@ -53,7 +53,8 @@ struct ChainShared {
     int n_amb;               // candidates whose order against the current winner the intervals leave open
     int sync_fail;           // a wait for another CTA's records ran out
     int pub_stop;            // stop bit of CTA 0's record for this step
-    int n_pairs;             // conflicting candidate pairs found for the walk
+    int n_pairs;             // walk: suspects / conflicting records / batches holding unsure candidates
+    int n_edges;             // walk: conflicting record pairs
     unsigned long long maxb; // max |b| over the entries (binary64 bits)
     unsigned int wmax;       // walk: bound on the running |b| (binary32 bits)
     long long red_l[32];
