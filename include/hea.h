@@ -107,6 +107,18 @@ hea_status hea_init_config(const hea_lattice* lat, int S, const int64_t* n_per, 
 hea_status hea_sro_counts(const hea_lattice* lat, int n_configs, const uint8_t* types, int S, int32_t* counts,
                           void* stream);
 
+/*
+ * hea_sro_counts with a chosen kernel (same arguments, results and errors):
+ *   method 0  automatic (bit planes for batches of at least 64 configurations when they apply)
+ *   method 1  neighbour gathers: per site, its shell histograms from species staged in shared memory,
+ *             summed per centre species across each warp
+ *   method 2  bit planes: per species one bit per site; N_ij^(k) = sum over shell-k vectors of
+ *             popcount(plane_i AND shifted plane_j), one CTA per configuration; needs Lx <= 64 and
+ *             2 <= S <= 6 (HEA_EINVAL otherwise)
+ */
+hea_status hea_sro_counts_method(const hea_lattice* lat, int n_configs, const uint8_t* types, int S, int32_t* counts,
+                                 int method, void* stream);
+
 /* Objective of Eq. fitness_function; all arrays in host memory, read during the call only. */
 typedef struct {
     int S;                 /* species, 2..8 */

@@ -279,14 +279,22 @@ hea_status hea_init_config(const hea_lattice* lat, int S, const int64_t* n_per, 
                        "hea_init_config launch");
 }
 
-hea_status hea_sro_counts(const hea_lattice* lat, int n_configs, const uint8_t* types, int S, int32_t* counts,
-                          void* stream) {
+hea_status hea_sro_counts_method(const hea_lattice* lat, int n_configs, const uint8_t* types, int S, int32_t* counts,
+                                 int method, void* stream) {
     if (!lat || !types || !counts) return fail(HEA_EINVAL, "NULL argument");
     if (S < 1 || S > HEA_MAX_SPECIES) return fail(HEA_EINVAL, "S = %d outside [1, %d]", S, HEA_MAX_SPECIES);
     if (n_configs < 1 || n_configs > 65535) return fail(HEA_EINVAL, "n_configs = %d outside [1, 65535]", n_configs);
+    if (method < 0 || method > 2) return fail(HEA_EINVAL, "method = %d outside [0, 2]", method);
+    if (method == 2 && !hea::sro_counts_planes_apply(lat->kind, lat->Lx, lat->Ly, lat->Lz, lat->M, S))
+        return fail(HEA_EINVAL, "the bit-plane recount needs Lx <= 64, 2 <= S <= 6 and its planes in shared memory");
     return cuda_status(hea::launch_sro_counts(lat->kind, lat->Lx, lat->Ly, lat->Lz, lat->M, S, n_configs, types,
-                                              counts, as_stream(stream)),
+                                              counts, method, as_stream(stream)),
                        "hea_sro_counts launch");
+}
+
+hea_status hea_sro_counts(const hea_lattice* lat, int n_configs, const uint8_t* types, int S, int32_t* counts,
+                          void* stream) {
+    return hea_sro_counts_method(lat, n_configs, types, S, counts, 0, stream);
 }
 
 hea_status hea_sro_alpha(const hea_lattice* lat, const hea_objective* obj, const int32_t* counts, double* alpha,

@@ -107,71 +107,324 @@ cudaError_t launch_init_config(int kind, int Lx, int Ly, int Lz, int S, const in
 }
 
 // ------------------------------------------------------------------------------------------------
-// Full recount of N_ij^(k) (Sec. 4.3).  Each thread takes sites, builds the per-shell neighbour
-// histogram of its site (8-bit fields per species, neighbours found from coordinates), and adds
-// the S fields of each shell to a CTA histogram in shared memory; the CTA histogram is flushed
-// to global memory with one atomic per nonzero bin.  grid.y indexes configurations.
+// Full recount of N_ij^(k) (Sec. 4.3): the number of ordered (site, shell vector) pairs whose sites
+// hold species i and j.  Two kernels:
+//
+//  * counts_gather_kernel: each thread builds the per-shell neighbour histogram of one site (8-bit
+//    fields per species, neighbours from coordinates) from species staged in shared memory -- the
+//    whole configuration when it fits, else a slab of conventional-cell planes with a halo -- or
+//    read through the cache when staging would leave too few CTAs.  A warp groups its lanes by the
+//    centre species (__match_any_sync) and sums each histogram field over the group
+//    (__reduce_add_sync) into a warp-private histogram: no atomics in the site loop.
+//  * counts_planes_kernel (rows of at most 64 cells, at most 6 species, one configuration per CTA):
+//    per species y a bit plane P_y (one 64-bit word per row of x-consecutive cells of one
+//    sublattice); the vector d maps row r of sublattice b to row r' of sublattice b' shifted by
+//    dcx cells along x, so sum_x [type = i][type(+d) = j] = popc(P_i[r] & rot(P_j[r'], dcx)).
+//    N_ij = N_ji (the shells are centrosymmetric), so only i <= j is counted.
+// grid.y (gather) or grid.x (planes) indexes configurations.
 // ------------------------------------------------------------------------------------------------
 constexpr int kCountThreads = 256;
+constexpr int kCountStageMax = 48 * 1024;   // bytes of species staged per CTA
 
-template <int KIND, int M>
-__global__ void __launch_bounds__(kCountThreads) sro_counts_kernel(Geo g, int S, const uint8_t* __restrict__ types,
-                                                                   int32_t* __restrict__ counts) {
-    extern __shared__ int32_t hist[];
+template <int KIND, int M, bool STAGED>
+__global__ void __launch_bounds__(kCountThreads) counts_gather_kernel(Geo g, Geo gt, int S, int tz, int hz,
+                                                                      const uint8_t* __restrict__ types,
+                                                                      int32_t* __restrict__ counts) {
+    extern __shared__ __align__(16) uint8_t sm[];
+    constexpr int B = KIND == kFCC ? 4 : 2;
     const int E = M * S * S;
-    for (int e = threadIdx.x; e < E; e += blockDim.x) hist[e] = 0;
-    __syncthreads();
-    const uint8_t* t = types + (size_t)blockIdx.y * (size_t)g.N;
-    auto onehot = [&](uint32_t n) -> uint64_t {
-        const int y = __ldg(t + n);
-        return y < S ? (1ull << (8 * y)) : 0ull;
-    };
-    for (uint32_t site = blockIdx.x * blockDim.x + threadIdx.x; site < (uint32_t)g.N;
-         site += gridDim.x * blockDim.x) {
-        const int A = __ldg(t + site);
-        if (A >= S) continue;
-        uint64_t h[M];
-        neighbour_histogram<KIND, M>(g, site, 0xFFFFFFFFu, onehot, h);
-#pragma unroll
-        for (int k = 0; k < M; ++k) {
-            int32_t* row = hist + (k * S + A) * S;
-            for (int y = 0; y < S; ++y) {
-                const int c = hist_field(h[k], y);
-                if (c) atomicAdd(row + y, c);
+    const int LxLy = g.LxLy, zt = tz + 2 * hz;
+    const int cfg = blockIdx.y, z0 = STAGED ? blockIdx.x * tz : 0;
+    const int tz_here = STAGED ? min(tz, g.Lz - z0) : 0;
+    const uint8_t* t = types + (size_t)cfg * (size_t)g.N;
+    const int nwarp = blockDim.x >> 5, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t staged = STAGED ? (uint32_t)(B * zt * LxLy) : 0u;
+    int32_t* wh = reinterpret_cast<int32_t*>(sm + align_up(staged, 16));
+    for (int i = threadIdx.x; i < nwarp * E; i += blockDim.x) wh[i] = 0;
+    if (STAGED) {
+        // planes z0 - hz .. z0 + tz + hz - 1 (periodic) of every sublattice, 16 bytes at a time when
+        // the planes are 16-byte aligned
+        const bool vec = ((reinterpret_cast<uintptr_t>(t) | (uintptr_t)LxLy | (uintptr_t)g.V) & 15u) == 0u;
+        for (int bp = 0; bp < B * zt; ++bp) {
+            const int b = bp / zt, p = bp - b * zt;
+            int zs = z0 - hz + p;
+            zs += (zs < 0) ? g.Lz : 0;
+            zs -= (zs >= g.Lz) ? g.Lz : 0;
+            const uint8_t* src = t + (size_t)b * g.V + (size_t)zs * LxLy;
+            uint8_t* dst = sm + (size_t)bp * LxLy;
+            if (vec) {
+                for (int i = threadIdx.x; i < LxLy / 16; i += blockDim.x)
+                    reinterpret_cast<uint4*>(dst)[i] = __ldg(reinterpret_cast<const uint4*>(src) + i);
+            } else {
+                for (int i = threadIdx.x; i < LxLy; i += blockDim.x) dst[i] = __ldg(src + i);
             }
         }
     }
     __syncthreads();
-    int32_t* out = counts + (size_t)blockIdx.y * (size_t)E;
-    for (int e = threadIdx.x; e < E; e += blockDim.x)
-        if (hist[e]) atomicAdd(out + e, hist[e]);
+    // staged: the sites of this tile (sublattice b, planes z0 .. z0 + tz_here - 1); through the cache:
+    // sites [blockIdx.x * tz, + tz) of the configuration (tz is then a count of sites)
+    const int n_here = STAGED ? B * tz_here * LxLy : max(0, min(tz, g.N - (int)blockIdx.x * tz));
+    const Divider dPlane = make_divider((uint32_t)(max(1, tz_here) * LxLy));
+    auto onehot = [&](uint32_t n) -> uint64_t {
+        const int y = STAGED ? sm[n] : __ldg(t + n);
+        return y < S ? (1ull << (8 * y)) : 0ull;
+    };
+    for (int base = warp * 32; base < n_here; base += blockDim.x) {
+        const int i = base + lane;
+        int A = 0xFF;
+        uint64_t h[M];
+#pragma unroll
+        for (int k = 0; k < M; ++k) h[k] = 0ull;
+        if (i < n_here) {
+            int X, Y, Z;
+            uint32_t own;
+            if (STAGED) {
+                const uint32_t b = divide((uint32_t)i, dPlane);
+                const uint32_t rem = (uint32_t)i - b * (uint32_t)(tz_here * LxLy);
+                const uint32_t czl = divide(rem, g.dLxLy);
+                const uint32_t rem2 = rem - czl * (uint32_t)LxLy;
+                const uint32_t cy = divide(rem2, g.dLx), cx = rem2 - cy * (uint32_t)g.Lx;
+                int ox, oy, oz;
+                if (KIND == kFCC) {
+                    ox = (int)(b >> 1);
+                    oy = (int)(b & 1);
+                    oz = ox ^ oy;
+                } else {
+                    ox = oy = oz = (int)b;
+                }
+                const int czs = (int)czl + hz;   // plane in the staged layout
+                own = b * (uint32_t)gt.V + (uint32_t)czs * (uint32_t)LxLy + cy * (uint32_t)g.Lx + cx;
+                X = 2 * (int)cx + ox;
+                Y = 2 * (int)cy + oy;
+                Z = 2 * czs + oz;
+            } else {
+                own = (uint32_t)blockIdx.x * (uint32_t)tz + (uint32_t)i;
+                site_coords<KIND>(g, own, X, Y, Z);
+            }
+            A = STAGED ? sm[own] : __ldg(t + own);
+            if (A < S)
+                neighbour_histogram_at<KIND, M, false, uint64_t>(STAGED ? gt : g, X, Y, Z, 0u, onehot, h, M);
+            else
+                A = 0xFF;
+        }
+        const unsigned grp = __match_any_sync(0xFFFFFFFFu, A);
+        const int leader = __ffs(grp) - 1;
+#pragma unroll
+        for (int k = 0; k < M; ++k)
+            for (int y = 0; y < S; ++y) {
+                const unsigned v = __reduce_add_sync(grp, (unsigned)hist_field(h[k], y));
+                if (lane == leader && A != 0xFF && v) wh[warp * E + (k * S + A) * S + y] += (int)v;
+            }
+    }
+    __syncthreads();
+    int32_t* out = counts + (size_t)cfg * (size_t)E;
+    for (int e = threadIdx.x; e < E; e += blockDim.x) {
+        int sum = 0;
+        for (int w = 0; w < nwarp; ++w) sum += wh[w * E + e];
+        if (sum) atomicAdd(out + e, sum);
+    }
+}
+
+// Rotation of the low `Lx` bits of w so that bit x of the result is bit (x + s) mod Lx of w
+// (|s| <= 2 < 2 Lx).
+template <typename W>
+__device__ __forceinline__ W rot_row(W w, int s, int Lx, W mask) {
+    s += (s < 0) ? Lx : 0;
+    s -= (s >= Lx) ? Lx : 0;
+    if (s == 0) return w;
+    return ((w >> s) | (w << (Lx - s))) & mask;
+}
+
+__device__ __forceinline__ int popc_w(uint32_t w) { return __popc(w); }
+__device__ __forceinline__ int popc_w(uint64_t w) { return __popcll(w); }
+
+template <int KIND, int S, typename W>
+__global__ void __launch_bounds__(kCountThreads) counts_planes_kernel(Geo g, int M, const uint8_t* __restrict__ types,
+                                                                      int32_t* __restrict__ counts) {
+    extern __shared__ __align__(16) uint8_t planes_raw[];
+    W* planes = reinterpret_cast<W*>(planes_raw);   // [S][R], one word per row (rows of at most 8 sizeof(W) cells)
+    constexpr int B = KIND == kFCC ? 4 : 2;
+    constexpr int NP = S * (S + 1) / 2;
+    const int Lx = g.Lx, Ly = g.Ly, Lz = g.Lz, R = B * Ly * Lz, E = M * S * S;
+    const uint8_t* t = types + (size_t)blockIdx.x * (size_t)g.N;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
+    const W mask = (Lx == 8 * (int)sizeof(W)) ? ~W(0) : (W)((W(1) << Lx) - W(1));
+    int32_t* wh = reinterpret_cast<int32_t*>(planes + (size_t)S * R);   // [nwarp][E]
+    for (int i = threadIdx.x; i < nwarp * E; i += blockDim.x) wh[i] = 0;
+    // bit planes: one warp per row, two halves of 32 cells
+    for (int r = warp; r < R; r += nwarp) {
+        const uint8_t* row = t + (size_t)r * Lx;   // rows are x-contiguous: ((b Lz + cz) Ly + cy) Lx
+        const int y0 = lane < Lx ? row[lane] : 0xFF;
+        const int y1 = lane + 32 < Lx ? row[lane + 32] : 0xFF;
+#pragma unroll
+        for (int y = 0; y < S; ++y) {
+            const uint32_t lo = __ballot_sync(0xFFFFFFFFu, y0 == y), hi = __ballot_sync(0xFFFFFFFFu, y1 == y);
+            if (lane == 0) planes[(size_t)y * R + r] = (W)((uint64_t)lo | ((uint64_t)hi << 32));
+        }
+    }
+    __syncthreads();
+    const ShellTable& TAB = c_shells[KIND];
+    const Divider dLy = make_divider((uint32_t)Ly), dLz = make_divider((uint32_t)Lz);
+    for (int base = warp * 32; base < R; base += blockDim.x) {
+        const int r = base + lane;
+        const bool act = r < R;
+        int b = 0, cz = 0, cy = 0;
+        if (act) {
+            const uint32_t t2 = divide((uint32_t)r, dLy);
+            cy = r - (int)t2 * Ly;
+            b = (int)divide(t2, dLz);
+            cz = (int)t2 - b * Lz;
+        }
+        int ox, oy, oz;
+        if (KIND == kFCC) {
+            ox = b >> 1;
+            oy = b & 1;
+            oz = ox ^ oy;
+        } else {
+            ox = oy = oz = b;
+        }
+        W own[S];
+#pragma unroll
+        for (int a = 0; a < S; ++a) own[a] = act ? planes[(size_t)a * R + r] : W(0);
+        for (int k = 0; k < M; ++k) {
+            int acc[NP];
+#pragma unroll
+            for (int x = 0; x < NP; ++x) acc[x] = 0;
+            for (int v = TAB.first[k]; v < TAB.first[k + 1]; ++v) {
+                // neighbour offsets in half units -> sublattice and cell offsets of the target row
+                const int hx = ox + TAB.v[v][0], hy = oy + TAB.v[v][1], hzz = oz + TAB.v[v][2];
+                const int dcx = hx >> 1, dcy = hy >> 1, dcz = hzz >> 1;   // floor division by 2
+                const int px = hx & 1, py = hy & 1;
+                const int b2 = (KIND == kFCC) ? 2 * px + py : px;
+                int cy2 = cy + dcy, cz2 = cz + dcz;
+                cy2 += (cy2 < 0) ? Ly : 0;
+                cy2 -= (cy2 >= Ly) ? Ly : 0;
+                cz2 += (cz2 < 0) ? Lz : 0;
+                cz2 -= (cz2 >= Lz) ? Lz : 0;
+                const int r2 = (b2 * Lz + cz2) * Ly + cy2;
+                W nb[S];
+#pragma unroll
+                for (int y = 0; y < S; ++y) nb[y] = act ? rot_row<W>(planes[(size_t)y * R + r2], dcx, Lx, mask) : W(0);
+                int x = 0;
+#pragma unroll
+                for (int a = 0; a < S; ++a)
+#pragma unroll
+                    for (int y = a; y < S; ++y) acc[x++] += popc_w((W)(own[a] & nb[y]));
+            }
+            int x = 0;
+#pragma unroll
+            for (int a = 0; a < S; ++a)
+#pragma unroll
+                for (int y = a; y < S; ++y) {
+                    const unsigned sum = __reduce_add_sync(0xFFFFFFFFu, (unsigned)acc[x++]);
+                    if (lane == 0 && sum) {
+                        wh[warp * E + (k * S + a) * S + y] += (int)sum;
+                        if (y != a) wh[warp * E + (k * S + y) * S + a] += (int)sum;
+                    }
+                }
+        }
+    }
+    __syncthreads();
+    int32_t* out = counts + (size_t)blockIdx.x * (size_t)E;
+    for (int e = threadIdx.x; e < E; e += blockDim.x) {
+        int sum = 0;
+        for (int w = 0; w < nwarp; ++w) sum += wh[w * E + e];
+        out[e] = sum;
+    }
 }
 
 template <int KIND, int M>
-static cudaError_t launch_counts_t(const Geo& g, int S, int n_configs, const uint8_t* types, int32_t* counts,
+static cudaError_t launch_gather_t(const Geo& g, int S, int n_configs, const uint8_t* types, int32_t* counts,
                                    cudaStream_t stream) {
     int sms = 0, dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (sms <= 0) sms = 152;
-    const int per_cfg = (g.N + kCountThreads - 1) / kCountThreads;
-    // Enough CTAs to fill the GPU a few times over, but at least one site per thread.
-    int bx = per_cfg;
-    const int want = (sms * 8 + n_configs - 1) / n_configs;
-    if (bx > want) bx = want < 1 ? 1 : want;
-    dim3 grid(bx, n_configs);
-    const size_t smem = sizeof(int32_t) * M * S * S;
-    sro_counts_kernel<KIND, M><<<grid, kCountThreads, smem, stream>>>(g, S, types, counts);
+    constexpr int B = KIND == kFCC ? 4 : 2;
+    const int reach = build_shell_table(KIND).reach[M - 1];
+    const int hz = (reach + 1) / 2;
+    const size_t hist = sizeof(int32_t) * (kCountThreads / 32) * M * S * S;
+    // whole configurations when they fit; else slabs of tz planes with hz halo planes on each side
+    int tz = g.Lz, h = 0;
+    if ((size_t)g.N > (size_t)kCountStageMax) {
+        h = hz;
+        tz = (int)((size_t)kCountStageMax / ((size_t)B * g.LxLy)) - 2 * h;
+    }
+    const int tiles = tz >= 1 ? (g.Lz + tz - 1) / tz : 0;
+    if (tz >= 1 && (size_t)tiles * n_configs >= (size_t)sms) {
+        const Geo gt = make_geo(KIND, g.Lx, g.Ly, tz + 2 * h);
+        const size_t smem = align_up((uint32_t)(B * (tz + 2 * h) * g.LxLy), 16) + hist;
+        if (smem > 48 * 1024) {
+            const cudaError_t err = cudaFuncSetAttribute(counts_gather_kernel<KIND, M, true>,
+                                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (err != cudaSuccess) {
+                (void)cudaGetLastError();
+                return err;
+            }
+        }
+        counts_gather_kernel<KIND, M, true><<<dim3(tiles, n_configs), kCountThreads, smem, stream>>>(
+            g, gt, S, tz, h, types, counts);
+    } else {
+        // through the cache, chunks of sites: enough CTAs to fill the GPU a few times over
+        int chunk = kCountThreads * 8;
+        while (chunk > kCountThreads && (size_t)((g.N + chunk - 1) / chunk) * n_configs < (size_t)(4 * sms)) chunk /= 2;
+        counts_gather_kernel<KIND, M, false><<<dim3((g.N + chunk - 1) / chunk, n_configs), kCountThreads, hist,
+                                               stream>>>(g, g, S, chunk, 0, types, counts);
+    }
     return cudaGetLastError();
 }
 
+template <int KIND, int S, typename W>
+static cudaError_t launch_planes_w(const Geo& g, int M, int n_configs, const uint8_t* types, int32_t* counts,
+                                   cudaStream_t stream) {
+    constexpr int B = KIND == kFCC ? 4 : 2;
+    const size_t smem = sizeof(W) * S * B * g.Ly * g.Lz + sizeof(int32_t) * (kCountThreads / 32) * M * S * S;
+    cudaError_t err = cudaFuncSetAttribute(counts_planes_kernel<KIND, S, W>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (err != cudaSuccess) {
+        (void)cudaGetLastError();
+        return err;
+    }
+    counts_planes_kernel<KIND, S, W><<<n_configs, kCountThreads, smem, stream>>>(g, M, types, counts);
+    return cudaGetLastError();
+}
+
+template <int KIND, int S>
+static cudaError_t launch_planes_t(const Geo& g, int M, int n_configs, const uint8_t* types, int32_t* counts,
+                                   cudaStream_t stream) {
+    if (g.Lx <= 32) return launch_planes_w<KIND, S, uint32_t>(g, M, n_configs, types, counts, stream);
+    return launch_planes_w<KIND, S, uint64_t>(g, M, n_configs, types, counts, stream);
+}
+
+// Shared memory of the bit-plane kernel, or 0 when it does not apply.
+static size_t planes_smem(int kind, int Lx, int Ly, int Lz, int M, int S) {
+    if (Lx > 64 || S < 2 || S > 6) return 0;
+    const int B = kind == kFCC ? 4 : 2;
+    const size_t smem = sizeof(uint64_t) * S * B * Ly * Lz + sizeof(int32_t) * (kCountThreads / 32) * M * S * S;
+    return smem <= 200 * 1024 ? smem : 0;
+}
+
+bool sro_counts_planes_apply(int kind, int Lx, int Ly, int Lz, int M, int S) {
+    return planes_smem(kind, Lx, Ly, Lz, M, S) != 0;
+}
+
 cudaError_t launch_sro_counts(int kind, int Lx, int Ly, int Lz, int M, int S, int n_configs, const uint8_t* types,
-                              int32_t* counts, cudaStream_t stream) {
+                              int32_t* counts, int method, cudaStream_t stream) {
     const Geo g = make_geo(kind, Lx, Ly, Lz);
+    const bool planes = (method == 2) || (method == 0 && planes_smem(kind, Lx, Ly, Lz, M, S) != 0 && n_configs >= 64);
+    if (planes) {
+#define HEA_PLANES_CASE(KD, SS) \
+    if (kind == KD && S == SS) return launch_planes_t<KD, SS>(g, M, n_configs, types, counts, stream);
+        HEA_PLANES_CASE(kFCC, 2) HEA_PLANES_CASE(kFCC, 3) HEA_PLANES_CASE(kFCC, 4) HEA_PLANES_CASE(kFCC, 5)
+        HEA_PLANES_CASE(kFCC, 6) HEA_PLANES_CASE(kBCC, 2) HEA_PLANES_CASE(kBCC, 3) HEA_PLANES_CASE(kBCC, 4)
+        HEA_PLANES_CASE(kBCC, 5) HEA_PLANES_CASE(kBCC, 6)
+#undef HEA_PLANES_CASE
+        return cudaErrorInvalidValue;
+    }
     cudaError_t err = cudaMemsetAsync(counts, 0, sizeof(int32_t) * (size_t)n_configs * M * S * S, stream);
     if (err != cudaSuccess) return err;
 #define HEA_COUNTS_CASE(KD, MM) \
-    if (kind == KD && M == MM) return launch_counts_t<KD, MM>(g, S, n_configs, types, counts, stream);
+    if (kind == KD && M == MM) return launch_gather_t<KD, MM>(g, S, n_configs, types, counts, stream);
     HEA_COUNTS_CASE(kFCC, 1) HEA_COUNTS_CASE(kFCC, 2) HEA_COUNTS_CASE(kFCC, 3) HEA_COUNTS_CASE(kFCC, 4)
     HEA_COUNTS_CASE(kFCC, 5) HEA_COUNTS_CASE(kBCC, 1) HEA_COUNTS_CASE(kBCC, 2) HEA_COUNTS_CASE(kBCC, 3)
     HEA_COUNTS_CASE(kBCC, 4) HEA_COUNTS_CASE(kBCC, 5)

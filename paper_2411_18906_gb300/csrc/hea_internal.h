@@ -204,7 +204,8 @@ hea_status set_last_error(hea_status status, const char* message);
 cudaError_t launch_init_config(int kind, int Lx, int Ly, int Lz, int S, const int64_t* cum, uint64_t seed,
                                uint8_t* types, cudaStream_t stream);
 cudaError_t launch_sro_counts(int kind, int Lx, int Ly, int Lz, int M, int S, int n_configs, const uint8_t* types,
-                              int32_t* counts, cudaStream_t stream);
+                              int32_t* counts, int method, cudaStream_t stream);
+bool sro_counts_planes_apply(int kind, int Lx, int Ly, int Lz, int M, int S);
 cudaError_t launch_sro_alpha(const ChainDesc& d, const int32_t* counts, double* alpha, double* f2,
                              cudaStream_t stream);
 cudaError_t launch_delta_swap(const ChainDesc& d, const uint8_t* types, const int32_t* counts,

@@ -73,6 +73,7 @@ def lib():
             "hea_shell_size": (i32, [P, i32]),
             "hea_init_config": (i32, [P, i32, P, u64, P, P]),
             "hea_sro_counts": (i32, [P, i32, P, i32, P, P]),
+            "hea_sro_counts_method": (i32, [P, i32, P, i32, P, i32, P]),
             "hea_sro_alpha": (i32, [P, ctypes.POINTER(hea_objective), P, P, P, P]),
             "hea_delta_swap": (i32, [P, ctypes.POINTER(hea_objective), P, P, P, i64, P, P, P]),
             "hea_search": (i32, [P, ctypes.POINTER(hea_objective), ctypes.POINTER(hea_search_params), P, P, P, P]),
@@ -172,6 +173,11 @@ def hea_init_config(lat, n_per, seed, types, stream=None):
 
 def hea_sro_counts(lat, n_configs, types, S, counts, stream=None):
     _check(lib().hea_sro_counts(lat.handle, int(n_configs), _ptr(types), int(S), _ptr(counts), _stream(stream)))
+
+
+def hea_sro_counts_method(lat, n_configs, types, S, counts, method, stream=None):
+    _check(lib().hea_sro_counts_method(lat.handle, int(n_configs), _ptr(types), int(S), _ptr(counts), int(method),
+                                       _stream(stream)))
 
 
 def hea_sro_alpha(lat, obj, counts, alpha, f2, stream=None):
