@@ -3,8 +3,8 @@
 A plain, slow, serial C++ implementation (hea_oracle.cpp) of what the GPU path computes:
 Warren-Cowley pair counts and alpha (Sec. 4.3, Eq. sro), the fitness (Sec. 4.4,
 Eq. fitness_function), the incremental swap delta (Sec. 4.5) and the parallel Monte Carlo
-search with depth termination (Sec. 4.2, Alg. parallel_mc; Sec. 4.6.4), plus the annealed-target
-input recipe.  Only tests/, the smoke check and the benchmark's CPU-baseline leg may import this
+search with depth termination (Sec. 4.2, Alg. parallel_mc; Sec. 4.6.4), the global search over a
+ranked pool of solutions (Sec. 4.1, Alg. global_search), plus the annealed-target input recipe.  Only tests/, the smoke check and the benchmark's CPU-baseline leg may import this
 package; the CUDA library neither imports nor links it.
 
 Every function here is argument marshalling around the C entry points.
@@ -37,6 +37,25 @@ class SearchParams(ctypes.Structure):
         ("group_top", ctypes.c_int32),
         ("check", ctypes.c_int32),
     ]
+
+
+class GlobalParams(ctypes.Structure):
+    _fields_ = [
+        ("n_solutions", ctypes.c_int32),
+        ("n_refine", ctypes.c_int32),
+        ("n_keep", ctypes.c_int32),
+        ("iterations", ctypes.c_int32),
+        ("tasks", ctypes.c_int32),
+        ("depth_limit", ctypes.c_int32),
+        ("max_steps", ctypes.c_int64),
+        ("seed", ctypes.c_uint64),
+        ("accept_mode", ctypes.c_int32),
+        ("check", ctypes.c_int32),
+    ]
+
+
+GLOBAL_LOG_DTYPE = np.dtype([("origin", np.int32), ("pad", np.int32), ("f2_in", np.float64),
+                             ("f2_out", np.float64), ("steps", np.int64), ("accepted", np.int64)])
 
 
 class SearchResult(ctypes.Structure):
@@ -81,6 +100,11 @@ def lib():
         _lib.or_search.argtypes = [i32, i32, i32, i32, i32, i32, P, P, P,
                                    ctypes.POINTER(SearchParams), P, P, ctypes.POINTER(SearchResult), P]
         _lib.or_search.restype = i32
+        _lib.or_fresh_seed.argtypes = [u64, u32, u32]
+        _lib.or_fresh_seed.restype = u64
+        _lib.or_global_search.argtypes = [i32, i32, i32, i32, i32, i32, P, P, P, ctypes.POINTER(GlobalParams),
+                                          P, P, P, P, P]
+        _lib.or_global_search.restype = i32
         _lib.or_anneal.argtypes = [i32, i32, i32, i32, i32, P, u64, dbl, i32, i32, P, P, P, P]
         _lib.or_anneal.restype = i32
         _lib.or_energy.argtypes = [i32, i32, i32, i32, i32, P, P]
@@ -207,6 +231,34 @@ def search(kind, L, M, n_per, w, target, types, cnt, *, K, max_steps, accept_mod
     if log:
         acc = acc[: res["accepted"]].copy()
     return ty, c, res, acc
+
+
+def fresh_seed(seed, g, j):
+    """Seed of fresh solution j of global-search iteration g."""
+    return int(lib().or_fresh_seed(seed, g, j))
+
+
+def global_search(kind, L, M, n_per, w, target, *, n_solutions, n_refine=0, n_keep=-1, iterations, tasks,
+                  depth_limit, max_steps=1 << 30, seed=1, accept_mode=0, check=False):
+    """Alg. global_search; returns (types[P_ls][N], counts[P_ls][M][S][S], f2[P_ls], log[G][P_ls],
+    totals (steps, trials, accepted)).  n_refine 0 = all P solutions; n_keep -1 = n_refine // 2."""
+    n = np.ascontiguousarray(n_per, dtype=np.int64)
+    S = len(n)
+    N = num_sites(kind, L)
+    w = np.ascontiguousarray(w, dtype=np.float64)
+    t = np.ascontiguousarray(target, dtype=np.float64).reshape(M, S, S)
+    PL = n_refine if n_refine > 0 else n_solutions
+    R = n_keep if n_keep >= 0 else PL // 2
+    gp = GlobalParams(n_solutions, PL, R, iterations, tasks, depth_limit, max_steps, seed, accept_mode,
+                      1 if check else 0)
+    types = np.zeros((PL, N), np.uint8)
+    cnt = np.zeros((PL, M, S, S), np.int32)
+    f2 = np.zeros(PL, np.float64)
+    log = np.zeros((iterations, PL), GLOBAL_LOG_DTYPE)
+    totals = np.zeros(3, np.int64)
+    _check(lib().or_global_search(kind, *L, M, S, _ptr(n), _ptr(w), _ptr(t), ctypes.byref(gp), _ptr(types),
+                                  _ptr(cnt), _ptr(f2), _ptr(log), _ptr(totals)), "global_search")
+    return types, cnt, f2, log, tuple(int(x) for x in totals)
 
 
 def anneal(kind, L, n_per, seed, T=800.0, sweeps=200, M_out=3):

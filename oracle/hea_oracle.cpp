@@ -17,6 +17,9 @@
 //   * Parallel Monte Carlo: K tasks each propose one random two-atom swap, the best change is
 //     taken, a depth counter counts non-improving rounds             (Sec. 4.2, Alg. parallel_mc)
 //   * Depth / step-budget termination                                (Sec. 4.2, Sec. 4.6.4)
+//   * Global search: a ranked pool of solutions, fresh random ones each iteration, the best
+//     refined by the parallel Monte Carlo search, the worst fraction discarded
+//                                                                    (Sec. 4.1, Alg. global_search)
 //   * Random numbers: Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11), written here from
 //     that paper's definition.
 //
@@ -674,6 +677,152 @@ int or_search(int kind, int Lx, int Ly, int Lz, int M, int S, const int64_t* n_p
     res->f2 = objective_f2(ob, counts);
     res->f = std::sqrt(res->f2);
     return status;
+}
+
+// ------------------------------------------------------------------------------------------------
+// Global search (Sec. 4.1, Alg. global_search).  Readings where the paper leaves a choice open:
+//   * Each iteration ranks P solutions: the R solutions kept from the previous iteration (none in
+//     the first) and P - R new ones, each a fresh random configuration ("random perturbation": the
+//     paper generates new solutions at random in every iteration, the first one entirely so).
+//   * Fitness of every solution = F^2 from a full recount; ranking = ascending (F^2, pool index),
+//     the kept solutions occupying pool indices 0..R-1 in their rank order, fresh one j index R + j.
+//   * The best P_ls solutions of the ranking ("top solutions") are each refined by the parallel
+//     Monte Carlo search (Alg. parallel_mc) with T tasks, depth limit d and a step cap; refined
+//     slot r of iteration g runs chain g * 65536 + r from step 0 and depth 0.
+//   * The refined solutions are ranked by (F^2, slot); the worst fraction p_a = 1 - R / P_ls is
+//     discarded and the best R are kept (R <= P_ls / 2: at most half of the refined set).
+//   * Fresh solution j of iteration g starts from the initial configuration with the 64-bit seed
+//     (r1 << 32) | r0 of Philox counter (j, g, 0, 4) under the search's key.
+// The result is the last iteration's refined set, ranked best first.
+// ------------------------------------------------------------------------------------------------
+struct or_global_params {
+    int32_t n_solutions;   // P: solutions ranked per iteration
+    int32_t n_refine;      // P_ls: best-ranked solutions refined per iteration (<= P)
+    int32_t n_keep;        // R: refined solutions kept for the next iteration (<= P_ls / 2)
+    int32_t iterations;    // G
+    int32_t tasks;         // T: candidate swaps per Monte Carlo step
+    int32_t depth_limit;   // d: a refinement ends after d consecutive steps without an accepted swap
+    int64_t max_steps;     // step cap of one refinement
+    uint64_t seed;
+    int32_t accept_mode;   // 0 best-of-T, 1 multi-accept
+    int32_t check;         // 1 = full recount after every Monte Carlo step
+};
+
+// One record per (iteration, refined slot).
+struct or_global_log {
+    int32_t origin;     // pool index the slot was selected from (< R: kept solution of that rank)
+    int32_t pad;
+    double f2_in;       // F^2 before the refinement
+    double f2_out;      // F^2 after it
+    int64_t steps;      // Monte Carlo steps of the refinement
+    int64_t accepted;   // swaps it accepted
+};
+
+// Seed of fresh solution j of iteration g.
+uint64_t or_fresh_seed(uint64_t seed, uint32_t g, uint32_t j) {
+    uint32_t r[4];
+    philox(seed, j, g, 0u, 4u, r);
+    return ((uint64_t)r[1] << 32) | (uint64_t)r[0];
+}
+
+// types_out[P_ls][N], counts_out[P_ls][M][S][S], f2_out[P_ls]: the final refined set, best first.
+// log[G][P_ls] (may be null).  totals[3] = Monte Carlo steps, trials and accepted swaps summed over
+// every refinement (may be null).
+int or_global_search(int kind, int Lx, int Ly, int Lz, int M, int S, const int64_t* n_per, const double* w,
+                     const double* target, const or_global_params* gp, uint8_t* types_out, int32_t* counts_out,
+                     double* f2_out, or_global_log* log, int64_t* totals) {
+    Geom geo;
+    Shells sh;
+    Objective ob;
+    if (!make_geom(kind, Lx, Ly, Lz, &geo) || !make_shells(geo, M, &sh) ||
+        !make_objective(geo, sh, S, n_per, w, target, &ob))
+        return OR_EINVAL;
+    const int P = gp->n_solutions, PL = gp->n_refine, R = gp->n_keep, G = gp->iterations;
+    if (P < 1 || PL < 1 || PL > P || R < 0 || 2 * R > PL || G < 1 || G > 65536 || PL > 65536 ||
+        gp->tasks < 1 || gp->depth_limit < 1 || gp->max_steps < 1)
+        return OR_EINVAL;
+    const int64_t N = geo.N;
+    const int E = M * S * S;
+    struct Solution {
+        std::vector<uint8_t> types;
+        std::vector<int32_t> counts;
+        double f2;
+    };
+    std::vector<Solution> kept;  // the R best refined solutions of the previous iteration, best first
+    std::vector<Solution> refined;
+    int64_t steps = 0, trials = 0, accepted = 0;
+    for (int it = 0; it < G; ++it) {
+        // New solutions: fresh random configurations after the kept ones.
+        std::vector<Solution> pool = kept;
+        const int n_kept = (int)kept.size();
+        for (int j = 0; j < P - n_kept; ++j) {
+            Solution x;
+            x.types.resize((size_t)N);
+            int rc = or_init_config(N, S, n_per, or_fresh_seed(gp->seed, (uint32_t)it, (uint32_t)j), x.types.data());
+            if (rc != OR_OK) return rc;
+            pool.push_back(std::move(x));
+        }
+        // Fitness of every solution from a full recount.
+        for (int i = n_kept; i < P; ++i) {
+            pool[i].counts.assign(E, 0);
+            full_counts(geo, sh, S, pool[i].types.data(), pool[i].counts.data());
+            pool[i].f2 = objective_f2(ob, pool[i].counts.data());
+        }
+        // Top solutions: the P_ls best by (F^2, pool index).
+        std::vector<int> order(P);
+        for (int i = 0; i < P; ++i) order[i] = i;
+        std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return pool[a].f2 < pool[b].f2; });
+        refined.clear();
+        for (int r = 0; r < PL; ++r) refined.push_back(pool[order[r]]);
+        // Local search on each top solution.
+        for (int r = 0; r < PL; ++r) {
+            or_search_params sp{};
+            sp.K = gp->tasks;
+            sp.accept_mode = gp->accept_mode;
+            sp.max_steps = gp->max_steps;
+            sp.depth_limit = gp->depth_limit;
+            sp.seed = gp->seed;
+            sp.chain = (uint32_t)it * 65536u + (uint32_t)r;
+            sp.check = gp->check;
+            or_search_result res{};
+            const double f2_in = refined[r].f2;
+            int rc = or_search(kind, Lx, Ly, Lz, M, S, n_per, w, target, &sp, refined[r].types.data(),
+                               refined[r].counts.data(), &res, nullptr);
+            if (rc != OR_OK) return rc;
+            refined[r].f2 = res.f2;
+            steps += res.steps;
+            trials += res.trials;
+            accepted += res.accepted;
+            if (log) {
+                or_global_log& L = log[(size_t)it * PL + r];
+                L.origin = order[r];
+                L.pad = 0;
+                L.f2_in = f2_in;
+                L.f2_out = res.f2;
+                L.steps = res.steps;
+                L.accepted = res.accepted;
+            }
+        }
+        // Rank the refined solutions; discard the worst fraction, keep the best R.
+        std::vector<int> rank(PL);
+        for (int r = 0; r < PL; ++r) rank[r] = r;
+        std::stable_sort(rank.begin(), rank.end(), [&](int a, int b) { return refined[a].f2 < refined[b].f2; });
+        std::vector<Solution> ranked;
+        for (int r = 0; r < PL; ++r) ranked.push_back(refined[rank[r]]);
+        refined.swap(ranked);
+        kept.assign(refined.begin(), refined.begin() + R);
+    }
+    for (int r = 0; r < PL; ++r) {
+        std::memcpy(types_out + (size_t)r * N, refined[r].types.data(), (size_t)N);
+        std::memcpy(counts_out + (size_t)r * E, refined[r].counts.data(), sizeof(int32_t) * E);
+        f2_out[r] = refined[r].f2;
+    }
+    if (totals) {
+        totals[0] = steps;
+        totals[1] = trials;
+        totals[2] = accepted;
+    }
+    return OR_OK;
 }
 
 // ------------------------------------------------------------------------------------------------
