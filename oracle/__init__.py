@@ -4,7 +4,8 @@ A plain, slow, serial C++ implementation (hea_oracle.cpp) of what the GPU path c
 Warren-Cowley pair counts and alpha (Sec. 4.3, Eq. sro), the fitness (Sec. 4.4,
 Eq. fitness_function), the incremental swap delta (Sec. 4.5) and the parallel Monte Carlo
 search with depth termination (Sec. 4.2, Alg. parallel_mc; Sec. 4.6.4), the global search over a
-ranked pool of solutions (Sec. 4.1, Alg. global_search), plus the annealed-target input recipe.  Only tests/, the smoke check and the benchmark's CPU-baseline leg may import this
+ranked pool of solutions (Sec. 4.1, Alg. global_search), the mapping of an external structure onto
+the lattice (Sec. 2.3), plus the annealed-target input recipe.  Only tests/, the smoke check and the benchmark's CPU-baseline leg may import this
 package; the CUDA library neither imports nor links it.
 
 Every function here is argument marshalling around the C entry points.
@@ -100,6 +101,8 @@ def lib():
         _lib.or_search.argtypes = [i32, i32, i32, i32, i32, i32, P, P, P,
                                    ctypes.POINTER(SearchParams), P, P, ctypes.POINTER(SearchResult), P]
         _lib.or_search.restype = i32
+        _lib.or_map_structure.argtypes = [i32, i32, i32, i32, i32, i64, P, P, dbl, P, dbl, P, P]
+        _lib.or_map_structure.restype = i32
         _lib.or_fresh_seed.argtypes = [u64, u32, u32]
         _lib.or_fresh_seed.restype = u64
         _lib.or_global_search.argtypes = [i32, i32, i32, i32, i32, i32, P, P, P, ctypes.POINTER(GlobalParams),
@@ -231,6 +234,19 @@ def search(kind, L, M, n_per, w, target, types, cnt, *, K, max_steps, accept_mod
     if log:
         acc = acc[: res["accepted"]].copy()
     return ty, c, res, acc
+
+
+def map_structure(kind, L, S, xyz, species, a, origin=(0.0, 0.0, 0.0), tol=0.25):
+    """External structure onto the lattice by nearest site; returns (types[N], report[4]:
+    off-lattice atoms, multiply taken sites, empty sites, bad species)."""
+    x = np.ascontiguousarray(xyz, dtype=np.float64).reshape(-1, 3)
+    sp = np.ascontiguousarray(species, dtype=np.uint8)
+    o = np.ascontiguousarray(origin, dtype=np.float64)
+    types = np.zeros(num_sites(kind, L), np.uint8)
+    report = np.zeros(4, np.int64)
+    _check(lib().or_map_structure(kind, *L, S, x.shape[0], _ptr(x), _ptr(sp), a, _ptr(o), tol, _ptr(types),
+                                  _ptr(report)), "map_structure")
+    return types, report
 
 
 def fresh_seed(seed, g, j):

@@ -17,6 +17,7 @@
 //   * Parallel Monte Carlo: K tasks each propose one random two-atom swap, the best change is
 //     taken, a depth counter counts non-improving rounds             (Sec. 4.2, Alg. parallel_mc)
 //   * Depth / step-budget termination                                (Sec. 4.2, Sec. 4.6.4)
+//   * An external structure mapped onto the lattice (nearest site)   (Sec. 2.3, application workflow)
 //   * Global search: a ranked pool of solutions, fresh random ones each iteration, the best
 //     refined by the parallel Monte Carlo search, the worst fraction discarded
 //                                                                    (Sec. 4.1, Alg. global_search)
@@ -677,6 +678,57 @@ int or_search(int kind, int Lx, int Ly, int Lz, int M, int S, const int64_t* n_p
     res->f2 = objective_f2(ob, counts);
     res->f = std::sqrt(res->f2);
     return status;
+}
+
+// ------------------------------------------------------------------------------------------------
+// External structure onto the lattice (Sec. 2.3, application workflow: a structure simulated by
+// an external tool is analysed to give the target SRO).  Atom i at Cartesian position xyz[i]
+// (cubic lattice constant a, the cell's origin at origin[]) goes to the lattice site nearest to
+// it under periodic boundaries, found by comparing its minimum-image distance to every site.
+// Reading: an atom farther than tol * a / 2 from its nearest site is off-lattice; a site taken by
+// two atoms or by none, and a species outside 0..S-1, are errors.  report[4] = off-lattice atoms,
+// sites taken more than once, empty sites, bad species; types[site] receives the species of the
+// (last) atom at that site.
+// ------------------------------------------------------------------------------------------------
+int or_map_structure(int kind, int Lx, int Ly, int Lz, int S, int64_t n, const double* xyz, const uint8_t* species,
+                     double a, const double* origin, double tol, uint8_t* types, int64_t* report) {
+    Geom g;
+    if (!make_geom(kind, Lx, Ly, Lz, &g) || !(a > 0.0) || !(tol >= 0.0) || n < 0) return OR_EINVAL;
+    std::vector<int> taken((size_t)g.N, 0);
+    for (int r = 0; r < 4; ++r) report[r] = 0;
+    for (int64_t s = 0; s < g.N; ++s) types[s] = 0;
+    const double half = 0.5 * a;
+    for (int64_t i = 0; i < n; ++i) {
+        int64_t best = -1;
+        double best_d2 = 0.0;
+        for (int64_t s = 0; s < g.N; ++s) {
+            int P[3];
+            site_position(g, s, P);
+            double d2 = 0.0;
+            for (int c = 0; c < 3; ++c) {
+                const double period = 2.0 * g.L[c];
+                double d = (xyz[3 * i + c] - origin[c]) / half - (double)P[c];
+                d -= period * std::floor(d / period + 0.5);  // minimum image
+                d2 += d * d;
+            }
+            if (best < 0 || d2 < best_d2) {
+                best = s;
+                best_d2 = d2;
+            }
+        }
+        if (best_d2 > tol * tol) {
+            report[0] += 1;
+            continue;
+        }
+        if (species[i] >= S) report[3] += 1;
+        taken[(size_t)best] += 1;
+        types[best] = species[i];
+    }
+    for (int64_t s = 0; s < g.N; ++s) {
+        if (taken[(size_t)s] > 1) report[1] += 1;
+        if (taken[(size_t)s] == 0) report[2] += 1;
+    }
+    return OR_OK;
 }
 
 // ------------------------------------------------------------------------------------------------
