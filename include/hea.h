@@ -269,6 +269,103 @@ hea_status hea_search_coop_noalloc(const hea_lattice* lat, const hea_objective* 
                                    int ctas, uint8_t* types, int32_t* counts, hea_search_result* result, void* stream);
 
 /* Message for the last error returned on the calling thread ("" if none). */
+/*
+ * External structure onto the lattice (Sec. 2.3, application workflow: a structure relaxed or
+ * simulated by an external tool is analysed to give the target SRO of a larger search; follow
+ * with hea_sro_counts and hea_sro_alpha).  Atom i at Cartesian position xyz[i] (length unit of
+ * the cubic lattice constant a; the cell's origin at origin[]) goes to the nearest lattice site:
+ * X = round(2 (x - origin_x) / a) taken modulo 2 Lx, likewise Y and Z, which is a site when its
+ * parities match the lattice (FCC: X + Y + Z even; BCC: all three equal).  types[site] receives
+ * species[i].  Counted in report (device int64[4], overwritten):
+ *   report[0]  atoms farther than tol half-lattice units (tol * a / 2) from that point, or whose
+ *              rounded point is not a site of this lattice (left unassigned)
+ *   report[1]  sites taken by more than one atom
+ *   report[2]  sites taken by no atom (their types entry is 0)
+ *   report[3]  atoms whose species is outside 0..S-1
+ * The mapping is valid when all four are 0.
+ *   xyz      device double[n][3];  species device uint8[n]
+ *   types    device uint8[N], out
+ *   scratch  device int32[N] (per-site claim counts)
+ *   origin   host double[3]
+ * Errors: HEA_EINVAL for n < 1, S outside 1..255, a <= 0, tol outside [0, 0.5] or non-finite
+ * origin; positions beyond 2^30 half units of the origin count as off-lattice.
+ */
+hea_status hea_map_structure(const hea_lattice* lat, int64_t n, const double* xyz, const uint8_t* species, int S,
+                             double a, const double* origin, double tol, uint8_t* types, int32_t* scratch,
+                             int64_t* report, void* stream);
+
+/*
+ * Global search (Sec. 4.1, Alg. global_search; the parameter ranges and the precision and
+ * performance presets are those of Sec. 2.1, parameter optimization): a pool of solutions ranked by
+ * fitness, the best refined by the parallel Monte Carlo search, the worst fraction discarded.
+ * Iteration g (0-based) of G:
+ *   1. pool = the n_keep solutions kept from iteration g-1 (none when g = 0), best first, then
+ *      P - (kept) fresh random configurations; fresh one j starts from the initial configuration
+ *      of hea_init_config with the 64-bit seed (r1 << 32) | r0 of Philox counter (j, g, 0, 4)
+ *      under the key (lo32(seed), hi32(seed));
+ *   2. F^2 of every fresh solution from a full recount;
+ *   3. the n_refine best of the pool by (F^2, pool index) are selected ("top solutions");
+ *   4. selected solution r is refined by the search of hea_search (K = tasks, accept_mode,
+ *      depth_limit, max_steps, seed, chain g * 65536 + r, step0 0, depth0 0);
+ *   5. the refined solutions are ranked by (F^2, r) and the best n_keep are kept; the others are
+ *      discarded (the fraction p_a = 1 - n_keep / n_refine; n_keep <= n_refine / 2 keeps at most
+ *      half, so at least half of every later refined set is new).
+ * The output is iteration G-1's refined set, ranked best first.  Every step runs on the device
+ * on `stream` (no host synchronisation inside the call, so it can be captured in a CUDA graph).
+ */
+typedef struct {
+    int32_t n_solutions;  /* P: solutions ranked per iteration, 1..4096 */
+    int32_t n_refine;     /* solutions refined per iteration, 1..P */
+    int32_t n_keep;       /* refined solutions kept for the next iteration, 0..n_refine/2 */
+    int32_t iterations;   /* G: 1..65536 */
+    int32_t tasks;        /* candidate swaps per Monte Carlo step, 1..4096 */
+    int32_t depth_limit;  /* a refinement ends after this many consecutive steps without an accepted swap, >= 1 */
+    int64_t max_steps;    /* step cap of one refinement, 1..2^32 */
+    uint64_t seed;        /* Philox key of the fresh solutions and of every refinement */
+    int32_t accept_mode;  /* 0: best-of-K (Alg. parallel_mc); 1: non-overlapping multi-accept */
+    int32_t reserved;     /* must be 0 */
+} hea_global_params;
+
+/* One record per (iteration, refined slot). */
+typedef struct {
+    int32_t origin;    /* pool index the slot was selected from (below the kept count: kept solution of that rank) */
+    int32_t pad;
+    double f2_in;      /* F^2 before the refinement */
+    double f2_out;     /* F^2 after the refinement */
+    int64_t steps;     /* Monte Carlo steps of the refinement */
+    int64_t accepted;  /* swaps it accepted */
+} hea_global_log;
+
+typedef struct {
+    int64_t steps;       /* Monte Carlo steps, summed over every refinement */
+    int64_t trials;      /* candidates scored, summed */
+    int64_t accepted;    /* swaps accepted, summed */
+    int32_t iterations;  /* iterations run (= G) */
+    int32_t status;      /* HEA_OK */
+    double best_f2;      /* F^2 of the best solution */
+    double best_f;       /* sqrt(best_f2) */
+} hea_global_result;
+
+/* Workspace for hea_global_search: the pool (P configurations with their counts and F^2), the
+ * selection order and the refinement descriptors.  0 for invalid arguments. */
+size_t hea_global_search_workspace_bytes(const hea_lattice* lat, const hea_objective* obj,
+                                         const hea_global_params* params);
+
+/*
+ *   types      device uint8[n_refine][N], out: the final refined set, best first
+ *   counts     device int32[n_refine][M][S][S], out: their counts
+ *   f2         device double[n_refine], out: their F^2
+ *   log        device hea_global_log[G][n_refine], out (NULL = not written)
+ *   result     device (or host-mapped) hea_global_result, out
+ *   workspace  device memory of at least hea_global_search_workspace_bytes() bytes, 256-byte
+ *              aligned, owned by the caller; calls sharing a workspace must not overlap
+ * Errors: HEA_EINVAL for parameters outside the ranges above or a short or misaligned workspace;
+ * HEA_ENOMEM when a cell with `tasks` candidate slots does not fit one CTA (as for hea_search).
+ */
+hea_status hea_global_search(const hea_lattice* lat, const hea_objective* obj, const hea_global_params* params,
+                             uint8_t* types, int32_t* counts, double* f2, hea_global_log* log,
+                             hea_global_result* result, void* workspace, size_t workspace_bytes, void* stream);
+
 const char* hea_last_error(void);
 const char* hea_status_string(int status);
 

@@ -194,6 +194,33 @@ hea_status place_coop(const hea_lattice* lat, int S, const hea_search_params* p,
                 (long long)lat->N, nrec);
 }
 
+// Global search: parameter ranges (see hea.h) and the search parameters of every refinement.
+hea_status check_global(const hea_lattice* lat, const hea_objective* obj, const hea_global_params* gp,
+                        hea_search_params* sp) {
+    if (!lat || !gp) return fail(HEA_EINVAL, "NULL argument");
+    hea_status st = check_objective(lat, obj);
+    if (st != HEA_OK) return st;
+    if (gp->n_solutions < 1 || gp->n_solutions > hea::kGlobalMaxSolutions)
+        return fail(HEA_EINVAL, "n_solutions = %d outside [1, %d]", gp->n_solutions, hea::kGlobalMaxSolutions);
+    if (gp->n_refine < 1 || gp->n_refine > gp->n_solutions)
+        return fail(HEA_EINVAL, "n_refine = %d outside [1, n_solutions = %d]", gp->n_refine, gp->n_solutions);
+    if (gp->n_keep < 0 || 2 * gp->n_keep > gp->n_refine)
+        return fail(HEA_EINVAL, "n_keep = %d outside [0, n_refine / 2]", gp->n_keep);
+    if (gp->iterations < 1 || gp->iterations > 65536) return fail(HEA_EINVAL, "iterations = %d outside [1, 65536]", gp->iterations);
+    if (gp->tasks < 1 || gp->tasks > hea::kMaxK) return fail(HEA_EINVAL, "tasks = %d outside [1, %d]", gp->tasks, hea::kMaxK);
+    if (gp->depth_limit < 1) return fail(HEA_EINVAL, "depth_limit must be >= 1");
+    if (gp->max_steps < 1 || gp->max_steps > (int64_t)1 << 32) return fail(HEA_EINVAL, "max_steps outside [1, 2^32]");
+    if (gp->accept_mode != 0 && gp->accept_mode != 1) return fail(HEA_EINVAL, "accept_mode must be 0 or 1");
+    if (gp->reserved != 0) return fail(HEA_EINVAL, "reserved field must be 0");
+    std::memset(sp, 0, sizeof *sp);
+    sp->K = gp->tasks;
+    sp->accept_mode = gp->accept_mode;
+    sp->max_steps = gp->max_steps;
+    sp->depth_limit = gp->depth_limit;
+    sp->seed = gp->seed;
+    return check_params(lat, sp);
+}
+
 // Plan = header + descriptors sorted by lattice kind (FCC first), then largest work first.
 struct PlanHeader {
     uint64_t magic;
@@ -459,6 +486,96 @@ hea_status hea_search_coop(const hea_lattice* lat, const hea_objective* obj, con
     const cudaError_t e = (d.kind == HEA_FCC) ? hea::launch_search_coop_fcc(d, as_stream(stream))
                                               : hea::launch_search_coop_bcc(d, as_stream(stream));
     return cuda_status(e, "hea_search_coop launch");
+}
+
+hea_status hea_map_structure(const hea_lattice* lat, int64_t n, const double* xyz, const uint8_t* species, int S,
+                             double a, const double* origin, double tol, uint8_t* types, int32_t* scratch,
+                             int64_t* report, void* stream) {
+    if (!lat || !xyz || !species || !origin || !types || !scratch || !report) return fail(HEA_EINVAL, "NULL argument");
+    if (n < 1) return fail(HEA_EINVAL, "n = %lld < 1", (long long)n);
+    if (S < 1 || S > 255) return fail(HEA_EINVAL, "S = %d outside [1, 255]", S);
+    if (!(a > 0.0) || !std::isfinite(a)) return fail(HEA_EINVAL, "lattice constant a must be finite and > 0");
+    if (!(tol >= 0.0 && tol <= 0.5)) return fail(HEA_EINVAL, "tol must be in [0, 0.5] half-lattice units");
+    for (int c = 0; c < 3; ++c)
+        if (!std::isfinite(origin[c])) return fail(HEA_EINVAL, "origin is not finite");
+    return cuda_status(hea::launch_map_structure(lat->kind, lat->Lx, lat->Ly, lat->Lz, n, xyz, species, S, a, origin,
+                                                 tol, types, scratch, report, as_stream(stream)),
+                       "hea_map_structure launch");
+}
+
+size_t hea_global_search_workspace_bytes(const hea_lattice* lat, const hea_objective* obj,
+                                         const hea_global_params* params) {
+    hea_search_params sp;
+    if (check_global(lat, obj, params, &sp) != HEA_OK) return 0;
+    const hea::GlobalLayout L = hea::global_layout(params->n_solutions, params->n_refine, lat->N,
+                                                   lat->M * obj->S * obj->S);
+    return L.total;
+}
+
+hea_status hea_global_search(const hea_lattice* lat, const hea_objective* obj, const hea_global_params* gp,
+                             uint8_t* types, int32_t* counts, double* f2, hea_global_log* log,
+                             hea_global_result* result, void* workspace, size_t workspace_bytes, void* stream) {
+    if (!types || !counts || !f2 || !result || !workspace) return fail(HEA_EINVAL, "NULL argument");
+    hea_search_params sp;
+    hea_status st = check_global(lat, obj, gp, &sp);
+    if (st != HEA_OK) return st;
+    const int P = gp->n_solutions, PL = gp->n_refine, R = gp->n_keep, G = gp->iterations, S = obj->S;
+    const int64_t N = lat->N;
+    const int E = lat->M * S * S;
+    const hea::GlobalLayout L = hea::global_layout(P, PL, N, E);
+    if (workspace_bytes < L.total)
+        return fail(HEA_EINVAL, "workspace of %zu bytes is smaller than the %zu needed", workspace_bytes, L.total);
+    if (reinterpret_cast<uintptr_t>(workspace) % 256 != 0) return fail(HEA_EINVAL, "workspace is not 256-byte aligned");
+    hea::ChainDesc d;
+    fill_desc(lat, obj, &d);
+    fill_params(&sp, &d);
+    st = place_chain(lat, S, &sp, sp.K, &d);
+    if (st != HEA_OK) return st;
+    d.ctas = 1;
+    std::vector<int64_t> cum(S + 1, 0);
+    for (int s = 0; s < S; ++s) cum[s + 1] = cum[s] + obj->n_per[s];
+
+    char* ws = static_cast<char*>(workspace);
+    uint8_t* pool_types = reinterpret_cast<uint8_t*>(ws + L.types);
+    int32_t* pool_counts = reinterpret_cast<int32_t*>(ws + L.counts);
+    double* pool_f2 = reinterpret_cast<double*>(ws + L.f2);
+    int32_t* order = reinterpret_cast<int32_t*>(ws + L.order);
+    hea::ChainDesc* descs = reinterpret_cast<hea::ChainDesc*>(ws + L.descs);
+    hea_search_result* res = reinterpret_cast<hea_search_result*>(ws + L.results);
+    cudaStream_t s = as_stream(stream);
+
+    cudaError_t e = cudaMemsetAsync(result, 0, sizeof *result, s);
+    for (int g = 0; g < G && e == cudaSuccess; ++g) {
+        const int kept = (g == 0) ? 0 : R;
+        const int fresh = P - kept;
+        hea_global_log* lg = log ? log + (size_t)g * PL : nullptr;
+        // 1-2: fresh random solutions after the kept ones, their counts and F^2.
+        if (fresh > 0) {
+            e = hea::launch_init_fresh(lat->kind, lat->Lx, lat->Ly, lat->Lz, S, cum.data(), gp->seed, (uint32_t)g, 0u,
+                                       fresh, pool_types + (size_t)kept * N, s);
+            if (e == cudaSuccess)
+                e = hea::launch_sro_counts(lat->kind, lat->Lx, lat->Ly, lat->Lz, lat->M, S, fresh,
+                                           pool_types + (size_t)kept * N, pool_counts + (size_t)kept * E, 0, s);
+            if (e == cudaSuccess) e = hea::launch_sro_alpha(d, pool_counts + (size_t)kept * E, nullptr, pool_f2 + kept, s, fresh);
+        }
+        // 3: the best n_refine into the output slots.
+        if (e == cudaSuccess) e = hea::launch_global_select(pool_f2, P, PL, order, lg, s);
+        if (e == cudaSuccess)
+            e = hea::launch_global_gather(pool_types, pool_counts, pool_f2, nullptr, order, PL, types, counts, f2, N, E, s);
+        // 4: one refinement chain per slot.
+        if (e == cudaSuccess) e = hea::launch_global_descs(d, descs, PL, types, counts, res, N, E, (uint32_t)g * 65536u, s);
+        if (e == cudaSuccess)
+            e = (d.kind == HEA_FCC) ? hea::launch_search_batch_fcc(descs, PL, d.smem_bytes, s)
+                                    : hea::launch_search_batch_bcc(descs, PL, d.smem_bytes, s);
+        // 5: rank the refined set, keep it in rank order at the front of the pool.
+        if (e == cudaSuccess) e = hea::launch_global_rank(res, PL, order, lg, result, s);
+        if (e == cudaSuccess)
+            e = hea::launch_global_gather(types, counts, nullptr, res, order, PL, pool_types, pool_counts, pool_f2, N, E, s);
+    }
+    if (e == cudaSuccess)
+        e = hea::launch_global_gather(pool_types, pool_counts, pool_f2, nullptr, nullptr, PL, types, counts, f2, N, E, s);
+    if (e == cudaSuccess) e = hea::launch_global_finish(pool_f2, G, result, s);
+    return cuda_status(e, "hea_global_search launch");
 }
 
 }  // extern "C"

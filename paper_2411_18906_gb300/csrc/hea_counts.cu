@@ -29,8 +29,8 @@ __device__ __forceinline__ uint64_t site_key(uint32_t i, uint32_t k0, uint32_t k
 constexpr int kInitThreads = 1024;
 constexpr int kInitMaxThresholds = 7;   // species 2..8 use the fast path
 
-__global__ void __launch_bounds__(kInitThreads) init_config_kernel(uint32_t N, int S, const Cum cum, uint32_t k0,
-                                                                   uint32_t k1, uint8_t* __restrict__ types) {
+__device__ void init_config_block(uint32_t N, int S, const Cum& cum, uint32_t k0, uint32_t k1,
+                                  uint8_t* __restrict__ types) {
     __shared__ uint32_t hist[kInitMaxThresholds][256];
     __shared__ uint64_t prefix[kInitMaxThresholds];
     __shared__ uint64_t remaining[kInitMaxThresholds];
@@ -79,6 +79,21 @@ __global__ void __launch_bounds__(kInitThreads) init_config_kernel(uint32_t N, i
     }
 }
 
+__global__ void __launch_bounds__(kInitThreads) init_config_kernel(uint32_t N, int S, const Cum cum, uint32_t k0,
+                                                                   uint32_t k1, uint8_t* __restrict__ types) {
+    init_config_block(N, S, cum, k0, k1, types);
+}
+
+// Fresh solutions of global-search iteration g (Sec. 4.1): configuration j (one CTA each) is the
+// initial configuration with the seed (r1 << 32) | r0 of Philox counter (j0 + j, g, 0, 4) under
+// the search's key; configurations are stored back to back (N bytes each).
+__global__ void __launch_bounds__(kInitThreads) init_fresh_kernel(uint32_t N, int S, const Cum cum, uint32_t k0,
+                                                                  uint32_t k1, uint32_t g, uint32_t j0,
+                                                                  uint8_t* __restrict__ types) {
+    const Rand4 r = philox(j0 + blockIdx.x, g, 0u, 4u, k0, k1);
+    init_config_block(N, S, cum, r.r0, r.r1, types + (size_t)blockIdx.x * N);
+}
+
 // Many species (S > 8): each site ranks itself against all keys (quadratic; small cells only).
 __global__ void init_config_rank_kernel(uint32_t N, int S, const Cum cum, uint32_t k0, uint32_t k1,
                                         uint8_t* __restrict__ types) {
@@ -103,6 +118,17 @@ cudaError_t launch_init_config(int kind, int Lx, int Ly, int Lz, int S, const in
     } else {
         init_config_rank_kernel<<<(N + 255) / 256, 256, 0, stream>>>(N, S, cum, k0, k1, types);
     }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_init_fresh(int kind, int Lx, int Ly, int Lz, int S, const int64_t* cum_host, uint64_t seed,
+                              uint32_t g, uint32_t j0, int n, uint8_t* types, cudaStream_t stream) {
+    const uint32_t N = (uint32_t)((kind == kFCC ? 4 : 2) * (int64_t)Lx * Ly * Lz);
+    if (S > kInitMaxThresholds + 1 || n < 1) return cudaErrorInvalidValue;
+    Cum cum{};
+    for (int s = 0; s <= S; ++s) cum.v[s] = cum_host[s];
+    init_fresh_kernel<<<n, kInitThreads, 0, stream>>>(N, S, cum, (uint32_t)(seed & 0xFFFFFFFFu),
+                                                       (uint32_t)(seed >> 32), g, j0, types);
     return cudaGetLastError();
 }
 
@@ -436,17 +462,21 @@ cudaError_t launch_sro_counts(int kind, int Lx, int Ly, int Lz, int M, int S, in
 // alpha_ij^(k) = 1 - n Q (Eq. sro, Q = N / ((Z_k N_i) N_j)) and F^2 = sum over (k,i,j) row-major of
 // w_k e^2, e = alpha - t (Eq. fitness_function).  One CTA; the sum runs serially in row-major order.
 // ------------------------------------------------------------------------------------------------
-__global__ void sro_alpha_kernel(const ChainDesc d, const int32_t* __restrict__ counts, double* __restrict__ alpha,
-                                 double* __restrict__ f2) {
+// One CTA per configuration: counts, alpha and f2 of configuration c at offsets c * E, c * E, c.
+__global__ void sro_alpha_kernel(const __grid_constant__ ChainDesc d, const int32_t* __restrict__ counts,
+                                 double* __restrict__ alpha, double* __restrict__ f2) {
     __shared__ double term[kMaxEntries];
     const int S = d.S, M = d.M, E = M * S * S;
     const ShellTable& T = c_shells[d.kind];
+    counts += (size_t)blockIdx.x * E;
+    if (alpha) alpha += (size_t)blockIdx.x * E;
+    f2 += blockIdx.x;
     for (int e = threadIdx.x; e < E; e += blockDim.x) {
         const int k = e / (S * S), i = (e / S) % S, j = e % S;
         const double den = __dmul_rn(__dmul_rn((double)T.z[k], (double)d.n_per[i]), (double)d.n_per[j]);
         const double Q = __ddiv_rn((double)d.N, den);
         const double a = __dsub_rn(1.0, __dmul_rn((double)counts[e], Q));
-        alpha[e] = a;
+        if (alpha) alpha[e] = a;
         const double err = __dsub_rn(a, d.target[e]);
         term[e] = __dmul_rn(d.w[k], __dmul_rn(err, err));
     }
@@ -459,8 +489,8 @@ __global__ void sro_alpha_kernel(const ChainDesc d, const int32_t* __restrict__ 
 }
 
 cudaError_t launch_sro_alpha(const ChainDesc& d, const int32_t* counts, double* alpha, double* f2,
-                             cudaStream_t stream) {
-    sro_alpha_kernel<<<1, 128, 0, stream>>>(d, counts, alpha, f2);
+                             cudaStream_t stream, int n_configs) {
+    sro_alpha_kernel<<<n_configs, 128, 0, stream>>>(d, counts, alpha, f2);
     return cudaGetLastError();
 }
 

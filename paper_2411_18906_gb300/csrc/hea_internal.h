@@ -11,6 +11,7 @@ namespace hea {
 constexpr int kChainThreads = 256;   // threads of a single-CTA search chain
 constexpr int kCoopThreads = 512;    // threads of each CTA of a cooperative chain
 constexpr int kMaxK = 4096;          // candidates per CTA per step (cooperative multi-accept: per chunk)
+constexpr int kGlobalMaxSolutions = 4096;  // global search: largest pool
 constexpr int kCoopMaxKc = 1 << 20;  // cooperative multi-accept: candidates per CTA per step
 constexpr int kCoopMaxTop = 4;       // records (best eligible candidates) per CTA per step
 constexpr int kPairWalkMax = 640;    // longest ranked list the pairwise multi-accept walk handles
@@ -197,17 +198,37 @@ __host__ __device__ inline size_t coop_workspace_bytes(int ctas) {
     return coop_records_offset(ctas) + 2 * (size_t)ctas * kCoopMaxTop * sizeof(CoopRecord);
 }
 
+// Global search workspace: the pool (P configurations, counts, F^2), the selection order, the
+// refinement descriptors and results; each part 256-byte aligned.
+struct GlobalLayout {
+    size_t types, counts, f2, order, descs, results, total;
+};
+inline GlobalLayout global_layout(int P, int PL, int64_t N, int E) {
+    auto up = [](size_t x) { return (x + 255) / 256 * 256; };
+    GlobalLayout L{};
+    L.types = 0;
+    L.counts = up((size_t)P * (size_t)N);
+    L.f2 = L.counts + up((size_t)P * E * sizeof(int32_t));
+    L.order = L.f2 + up((size_t)P * sizeof(double));
+    L.descs = L.order + up((size_t)P * sizeof(int32_t));
+    L.results = L.descs + up((size_t)PL * sizeof(ChainDesc));
+    L.total = L.results + up((size_t)PL * sizeof(hea_search_result));
+    return L;
+}
+
 // Records `message` as the calling thread's hea_last_error() text and returns `status`.
 hea_status set_last_error(hea_status status, const char* message);
 
 // Launchers implemented in the .cu files.
 cudaError_t launch_init_config(int kind, int Lx, int Ly, int Lz, int S, const int64_t* cum, uint64_t seed,
                                uint8_t* types, cudaStream_t stream);
+cudaError_t launch_init_fresh(int kind, int Lx, int Ly, int Lz, int S, const int64_t* cum, uint64_t seed,
+                              uint32_t g, uint32_t j0, int n, uint8_t* types, cudaStream_t stream);
 cudaError_t launch_sro_counts(int kind, int Lx, int Ly, int Lz, int M, int S, int n_configs, const uint8_t* types,
                               int32_t* counts, int method, cudaStream_t stream);
 bool sro_counts_planes_apply(int kind, int Lx, int Ly, int Lz, int M, int S);
 cudaError_t launch_sro_alpha(const ChainDesc& d, const int32_t* counts, double* alpha, double* f2,
-                             cudaStream_t stream);
+                             cudaStream_t stream, int n_configs = 1);
 cudaError_t launch_delta_swap(const ChainDesc& d, const uint8_t* types, const int32_t* counts,
                               const int64_t* pairs, int64_t K, double* key, int32_t* dcounts, cudaStream_t stream);
 cudaError_t launch_search_fcc(const ChainDesc& d, cudaStream_t stream);
@@ -216,6 +237,20 @@ cudaError_t launch_search_batch_fcc(const ChainDesc* descs_dev, int n, uint32_t 
 cudaError_t launch_search_batch_bcc(const ChainDesc* descs_dev, int n, uint32_t smem_max, cudaStream_t stream);
 cudaError_t launch_search_coop_fcc(const ChainDesc& d, cudaStream_t stream);
 cudaError_t launch_search_coop_bcc(const ChainDesc& d, cudaStream_t stream);
+cudaError_t launch_map_structure(int kind, int Lx, int Ly, int Lz, int64_t n, const double* xyz, const uint8_t* species,
+                                 int S, double a, const double* origin, double tol, uint8_t* types, int32_t* scratch,
+                                 int64_t* report, cudaStream_t stream);
+cudaError_t launch_global_select(const double* pool_f2, int P, int PL, int32_t* order, hea_global_log* log,
+                                 cudaStream_t stream);
+cudaError_t launch_global_rank(const hea_search_result* res, int PL, int32_t* order, hea_global_log* log,
+                               hea_global_result* total, cudaStream_t stream);
+cudaError_t launch_global_gather(const uint8_t* src_types, const int32_t* src_counts, const double* src_f2,
+                                 const hea_search_result* src_res, const int32_t* order, int n, uint8_t* dst_types,
+                                 int32_t* dst_counts, double* dst_f2, int64_t N, int E, cudaStream_t stream);
+cudaError_t launch_global_descs(const ChainDesc& d, ChainDesc* descs, int n, uint8_t* types, int32_t* counts,
+                                hea_search_result* results, int64_t N, int E, uint32_t chain_base,
+                                cudaStream_t stream);
+cudaError_t launch_global_finish(const double* best_f2, int G, hea_global_result* total, cudaStream_t stream);
 int coop_max_ctas_fcc(const ChainDesc& d);
 int coop_max_ctas_bcc(const ChainDesc& d);
 

@@ -47,6 +47,23 @@ class hea_search_result(ctypes.Structure):
                 ("f", ctypes.c_double)]
 
 
+class hea_global_params(ctypes.Structure):
+    _fields_ = [("n_solutions", ctypes.c_int32), ("n_refine", ctypes.c_int32), ("n_keep", ctypes.c_int32),
+                ("iterations", ctypes.c_int32), ("tasks", ctypes.c_int32), ("depth_limit", ctypes.c_int32),
+                ("max_steps", ctypes.c_int64), ("seed", ctypes.c_uint64), ("accept_mode", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
+class hea_global_result(ctypes.Structure):
+    _fields_ = [("steps", ctypes.c_int64), ("trials", ctypes.c_int64), ("accepted", ctypes.c_int64),
+                ("iterations", ctypes.c_int32), ("status", ctypes.c_int32), ("best_f2", ctypes.c_double),
+                ("best_f", ctypes.c_double)]
+
+
+# hea_global_log as a numpy record type.
+GLOBAL_LOG_DTYPE = np.dtype([("origin", np.int32), ("pad", np.int32), ("f2_in", np.float64),
+                             ("f2_out", np.float64), ("steps", np.int64), ("accepted", np.int64)])
+
 RESULT_BYTES = ctypes.sizeof(hea_search_result)
 RESULT_FIELDS = [f for f, _ in hea_search_result._fields_]
 
@@ -87,6 +104,11 @@ def lib():
                                       P, P, sz, P]),
             "hea_search_coop_noalloc": (i32, [P, ctypes.POINTER(hea_objective), ctypes.POINTER(hea_search_params),
                                               i32, P, P, P, P]),
+            "hea_map_structure": (i32, [P, i64, P, P, i32, ctypes.c_double, P, ctypes.c_double, P, P, P, P]),
+            "hea_global_search_workspace_bytes": (sz, [P, ctypes.POINTER(hea_objective),
+                                                       ctypes.POINTER(hea_global_params)]),
+            "hea_global_search": (i32, [P, ctypes.POINTER(hea_objective), ctypes.POINTER(hea_global_params), P, P, P,
+                                        P, P, P, sz, P]),
             "hea_last_error": (ctypes.c_char_p, []),
             "hea_status_string": (ctypes.c_char_p, [i32]),
         }
@@ -257,3 +279,35 @@ class BatchPlan:
 
 def hea_search_batch(plan_host, plan_dev, stream=None):
     _check(lib().hea_search_batch(_ptr(plan_host), _ptr(plan_dev), _stream(stream)))
+
+
+def global_params(n_solutions, iterations, tasks, depth_limit, n_refine=0, n_keep=-1, max_steps=1 << 30, seed=1,
+                  accept_mode=0):
+    """hea_global_params; n_refine 0 = all n_solutions, n_keep -1 = n_refine // 2 (p_a = 1/2)."""
+    PL = n_refine if n_refine > 0 else n_solutions
+    R = n_keep if n_keep >= 0 else PL // 2
+    return hea_global_params(n_solutions, PL, R, iterations, tasks, depth_limit, max_steps, seed, accept_mode, 0)
+
+
+def hea_global_search_workspace_bytes(lat, obj, params):
+    return int(lib().hea_global_search_workspace_bytes(lat.handle, ctypes.byref(obj.c), ctypes.byref(params)))
+
+
+def hea_global_search(lat, obj, params, types, counts, f2, log, result, workspace, stream=None):
+    """`result` is a device buffer of sizeof(hea_global_result) bytes; `log` a device buffer of
+    iterations * n_refine GLOBAL_LOG_DTYPE records or None; `workspace` 256-byte aligned."""
+    nbytes = workspace.numel() * workspace.element_size()
+    _check(lib().hea_global_search(lat.handle, ctypes.byref(obj.c), ctypes.byref(params), _ptr(types), _ptr(counts),
+                                   _ptr(f2), _ptr(log), _ptr(result), _ptr(workspace), nbytes, _stream(stream)))
+
+
+def decode_global_result(raw):
+    r = hea_global_result.from_buffer_copy(bytes(np.ascontiguousarray(raw, dtype=np.uint8)))
+    return {f: getattr(r, f) for f, _ in hea_global_result._fields_}
+
+
+def hea_map_structure(lat, n, xyz, species, S, a, origin, tol, types, scratch, report, stream=None):
+    """xyz, species, types, scratch, report: device tensors; origin: 3 floats (host)."""
+    o = np.ascontiguousarray(origin, dtype=np.float64)
+    _check(lib().hea_map_structure(lat.handle, int(n), _ptr(xyz), _ptr(species), int(S), float(a), _ptr(o),
+                                   float(tol), _ptr(types), _ptr(scratch), _ptr(report), _stream(stream)))

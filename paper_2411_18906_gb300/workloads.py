@@ -143,3 +143,11 @@ def batch_cells(n_cells: int = 512, seed: int = 1, n_lo: float = 500, n_hi: floa
         target = np.array(entry["alpha"])[:M]
         cells.append(CellSpec(kind, L, M, n_per, seed=1000 + c, target=target))
     return cells
+
+
+# Global-search parameter presets (Sec. 2.1, parameter optimization): solutions, global
+# iterations, tasks (candidate swaps per Monte Carlo step) and search depth.
+GLOBAL_PRESETS = {
+    "precision": dict(n_solutions=128, iterations=10, tasks=256, depth_limit=10),
+    "performance": dict(n_solutions=64, iterations=6, tasks=64, depth_limit=8),
+}

@@ -115,3 +115,30 @@ def gpu_search_coop(kind, L, M, n_per, w, target, types, cnt, ctas, **kw):
     hea.hea_search_coop(lat, obj, hea.search_params(**kw), ctas, t, c, res, ws)
     torch.cuda.synchronize()
     return t.cpu().numpy(), c.cpu().numpy(), hea.decode_results(res.cpu().numpy())[0]
+
+
+def gpu_global_search(kind, L, M, n_per, w, target, **kw):
+    """hea_global_search on fresh torch buffers; kw as hea.global_params.  Returns (types, counts,
+    f2, log, result dict) as numpy."""
+    ensure_built()
+    lat = hea.Lattice(kind, L, M)
+    obj = hea.Objective(n_per, w, target)
+    gp = hea.global_params(**kw)
+    S = len(n_per)
+    PL, G = gp.n_refine, gp.iterations
+    types = torch.empty((PL, lat.N), dtype=torch.uint8, device="cuda")
+    counts = torch.empty((PL, M, S, S), dtype=torch.int32, device="cuda")
+    f2 = torch.empty(PL, dtype=torch.float64, device="cuda")
+    log = torch.zeros(G * PL * hea.GLOBAL_LOG_DTYPE.itemsize, dtype=torch.uint8, device="cuda")
+    res = torch.zeros(ctypes_sizeof_global_result(), dtype=torch.uint8, device="cuda")
+    ws = torch.empty(hea.hea_global_search_workspace_bytes(lat, obj, gp), dtype=torch.uint8, device="cuda")
+    hea.hea_global_search(lat, obj, gp, types, counts, f2, log, res, ws)
+    torch.cuda.synchronize()
+    lg = np.frombuffer(log.cpu().numpy().tobytes(), dtype=hea.GLOBAL_LOG_DTYPE).reshape(G, PL)
+    return (types.cpu().numpy(), counts.cpu().numpy(), f2.cpu().numpy(), lg,
+            hea.decode_global_result(res.cpu().numpy()))
+
+
+def ctypes_sizeof_global_result():
+    import ctypes
+    return ctypes.sizeof(hea.hea_global_result)

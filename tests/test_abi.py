@@ -97,3 +97,49 @@ def test_search_rejects_cells_beyond_shared_memory(L):
 def test_batch_plan_layout(L):
     assert hea.hea_search_batch_plan_bytes(0) == 0
     assert hea.hea_search_batch_plan_bytes(3) > hea.hea_search_batch_plan_bytes(2) > 0
+
+
+class FakeBuf(FakePtr):
+    """A stand-in device buffer of a given size (validation reads only its size)."""
+
+    def __init__(self, nbytes, addr=0x100000):
+        self.nbytes, self.addr = nbytes, addr
+
+    def data_ptr(self):
+        return self.addr
+
+    def numel(self):
+        return self.nbytes
+
+    def element_size(self):
+        return 1
+
+
+def test_global_search_validation(L):
+    lat = hea.hea_build_lattice(hea.HEA_FCC, 4, 4, 4, 3)
+    obj = hea.Objective([64, 64, 64, 64], np.ones(3), np.zeros((3, 4, 4)))
+    good = hea.global_params(64, 6, 64, 8)
+    need = hea.hea_global_search_workspace_bytes(lat, obj, good)
+    # pool of 64 x 256 bytes + counts + F^2 + order + 32... descriptors and results
+    assert need >= 64 * 256 + 64 * 48 * 4 + 64 * 8 + 64 * 4
+    assert hea.hea_global_search_workspace_bytes(lat, obj, hea.global_params(128, 10, 256, 10)) > need
+    bad = [hea.global_params(0, 6, 64, 8), hea.global_params(5000, 6, 64, 8), hea.global_params(64, 0, 64, 8),
+           hea.global_params(64, 6, 0, 8), hea.global_params(64, 6, 5000, 8), hea.global_params(64, 6, 64, 0),
+           hea.global_params(64, 6, 64, 8, n_refine=65), hea.global_params(64, 6, 64, 8, n_refine=10, n_keep=6),
+           hea.global_params(64, 6, 64, 8, max_steps=0), hea.global_params(64, 6, 64, 8, accept_mode=2),
+           hea.global_params(64, 70000, 64, 8)]
+    b = FakePtr()
+    for p in bad:
+        assert hea.hea_global_search_workspace_bytes(lat, obj, p) == 0
+        assert _status(hea.hea_global_search, lat, obj, p, b, b, b, None, b, FakeBuf(need), 0) == hea.HEA_EINVAL
+    # short or misaligned workspace
+    assert _status(hea.hea_global_search, lat, obj, good, b, b, b, None, b, FakeBuf(need - 1), 0) == hea.HEA_EINVAL
+    assert _status(hea.hea_global_search, lat, obj, good, b, b, b, None, b, FakeBuf(need, 0x100010), 0) == hea.HEA_EINVAL
+    bad_n = hea.Objective([0, 64, 64, 128], np.ones(3), np.zeros((3, 4, 4)))
+    assert _status(hea.hea_global_search, lat, bad_n, good, b, b, b, None, b, FakeBuf(need), 0) == hea.HEA_EINVAL
+    # a cell with `tasks` candidate slots beyond one CTA's shared memory
+    big = hea.hea_build_lattice(hea.HEA_FCC, 50, 50, 50, 3)
+    obj5 = hea.Objective([big.N // 5] * 5, np.ones(3), np.zeros((3, 5, 5)))
+    p = hea.global_params(4, 1, 256, 8)
+    assert _status(hea.hea_global_search, big, obj5, p, b, b, b, None, b,
+                   FakeBuf(hea.hea_global_search_workspace_bytes(big, obj5, p)), 0) == hea.HEA_ENOMEM

@@ -102,7 +102,7 @@ def test_pool_selection_keep_and_discard(case):
         assert log["origin"][g].tolist() == expect, g
         for r in range(PL):
             assert log["f2_in"][g, r] == pool_f2[expect[r]], (g, r)
-            assert log["f2_out"][g, r] <= log["f2_in"][g, r]
+            assert log["f2_out"][g, r] <= log["f2_in"][g, r] * (1 + 1e-12)   # up to the key's rounding
         ranked_slots = sorted(range(PL), key=lambda r: (log["f2_out"][g, r], r))
         prev_ranked = [log["f2_out"][g, r] for r in ranked_slots]
     assert f2.tolist() == prev_ranked
@@ -118,7 +118,7 @@ def test_pool_selection_keep_and_discard(case):
 def test_best_never_rises_across_iterations():
     (_, _, _, _, _, _), (_, _, f2, log, _) = run_case((ind.BCC, (3, 3, 2), 2, [12, 12, 12], 12, 0, -1, 5, 6, 2, 0.5))
     best = log["f2_out"].min(axis=1)
-    assert all(best[g + 1] <= best[g] for g in range(len(best) - 1))
+    assert all(best[g + 1] <= best[g] * (1 + 1e-12) for g in range(len(best) - 1))
     assert f2[0] == best[-1]
 
 
