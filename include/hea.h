@@ -174,7 +174,8 @@ typedef struct {
     int32_t test_withhold_cta; /* testing aid of the cooperative search: 1 + the index of a CTA that
                                   never publishes its records, so that the others' bounded waits run
                                   out and the search ends with HEA_ESYNC (0 = none; must be 0 elsewhere) */
-    int32_t reserved;     /* must be 0 */
+    int32_t threads;      /* threads per CTA of hea_search and hea_search_batch: 0 (= 256), 128, 256 or 512
+                             (results do not depend on it); must be 0 for the cooperative searches */
 } hea_search_params;
 
 /* Written by the search on the device (device or host-mapped pinned memory). */
@@ -365,6 +366,16 @@ size_t hea_global_search_workspace_bytes(const hea_lattice* lat, const hea_objec
 hea_status hea_global_search(const hea_lattice* lat, const hea_objective* obj, const hea_global_params* params,
                              uint8_t* types, int32_t* counts, double* f2, hea_global_log* log,
                              hea_global_result* result, void* workspace, size_t workspace_bytes, void* stream);
+
+/*
+ * Measurement aid (not part of the search): the single-byte shared-memory gather rate of this GPU,
+ * the ceiling of the swap scoring's neighbour gathers.  Launches `ctas` CTAs of 512 threads, each
+ * holding a 64 KiB buffer in shared memory; every thread performs iters * 8 one-byte loads.
+ *   mode 0: random addresses (as the scoring's gathers are);  mode 1: lane l reads bank l.
+ *   sink: device uint64[2], caller-zeroed; sink[1] counts finished CTAs.
+ * Time the call with events; bytes gathered = ctas * 512 * 8 * iters.
+ */
+hea_status hea_probe_smem_gather(int mode, int ctas, int64_t iters, uint64_t* sink, void* stream);
 
 const char* hea_last_error(void);
 const char* hea_status_string(int status);

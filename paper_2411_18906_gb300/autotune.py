@@ -1,9 +1,13 @@
-"""Autotuner for the batched search: picks the candidates-per-step K of each cell-size bucket.
+"""Autotuner for the batched search: picks the candidates-per-step K and the threads per CTA of
+each cell-size bucket.
 
 For a fixed trial budget per cell, K trades steps (each with a fixed barrier/accept cost) against
-per-step work; the best K depends on the cell size and the GPU.  The tuner times hea_search_batch
-on a sample of the workload's cells for each K in a candidate set, per size bucket, and keeps the
-K with the highest trials/s.  Results are cached per (GPU name, bucket, budget) in a JSON file.
+per-step work, and the CTA's thread count trades parallel scoring against the per-step
+synchronisation; the best pair depends on the cell size and the GPU.  The tuner times
+hea_search_batch on a sample of the workload's cells for every (K, threads) pair of a candidate
+grid, per size bucket, skipping pairs whose candidate slots do not fit shared memory, and keeps the
+pair with the highest trials/s.  The report says whether the chosen K lies strictly inside the
+feasible K range (bracketed).  Results are cached per (GPU name, budget, grid) in a JSON file.
 """
 import json
 import os
@@ -13,7 +17,8 @@ import numpy as np
 
 from . import hea
 
-CANDIDATE_K = (128, 256, 512, 1024)
+CANDIDATE_K = (128, 256, 512, 1024, 2048, 4096)
+CANDIDATE_THREADS = (128, 256, 512)
 BUCKETS = ((0, 4000), (4000, 12000), (12000, 1 << 30))   # sites
 
 
@@ -29,16 +34,23 @@ def _cache_path():
     return os.path.join(root, "hea_gb300_autotune.json")
 
 
-def _time_batch(torch, cells, K, trials, accept_mode, repeats=2):
-    """Seconds of one hea_search_batch over `cells` (list of (Lattice, Objective, types, counts))."""
+def _time_batch(torch, cells, K, trials, accept_mode, threads=0, repeats=2):
+    """Seconds of one hea_search_batch over `cells` (list of (Lattice, Objective, types, counts));
+    None when the candidate slots do not fit a CTA's shared memory."""
     n = len(cells)
-    params = [hea.search_params(K, max(1, trials // K), accept_mode=accept_mode, seed=7 + i) for i in range(n)]
+    params = [hea.search_params(K, max(1, trials // K), accept_mode=accept_mode, seed=7 + i, threads=threads)
+              for i in range(n)]
     res = torch.zeros(n * hea.RESULT_BYTES, dtype=torch.uint8, device="cuda")
     best = None
     for _ in range(repeats):
         ts = [t.clone() for _, _, t, _ in cells]
         cs = [c.clone() for _, _, _, c in cells]
-        plan = hea.BatchPlan([l for l, _, _, _ in cells], [o for _, o, _, _ in cells], params, ts, cs, res)
+        try:
+            plan = hea.BatchPlan([l for l, _, _, _ in cells], [o for _, o, _, _ in cells], params, ts, cs, res)
+        except hea.HeaError as e:
+            if e.status == hea.HEA_ENOMEM:
+                return None
+            raise
         plan_dev = torch.from_numpy(plan.host).cuda()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -50,10 +62,11 @@ def _time_batch(torch, cells, K, trials, accept_mode, repeats=2):
 
 
 def tune(cells, trials: int, accept_mode: int = 0, sample: int = 48, use_cache: bool = True):
-    """cells: list of (Lattice, Objective, types tensor, counts tensor).  Returns ({bucket: K}, report)."""
+    """cells: list of (Lattice, Objective, types tensor, counts tensor).  Returns
+    ({bucket: (K, threads)}, report)."""
     import torch
     gpu = torch.cuda.get_device_name(0)
-    key = f"{gpu}|{trials}|{accept_mode}|{len(cells)}"
+    key = f"v2|{gpu}|{trials}|{accept_mode}|{len(cells)}|{CANDIDATE_K}|{CANDIDATE_THREADS}"
     path = _cache_path()
     cache = {}
     if use_cache and os.path.exists(path):
@@ -63,7 +76,7 @@ def tune(cells, trials: int, accept_mode: int = 0, sample: int = 48, use_cache: 
         except (OSError, ValueError):
             cache = {}
     if use_cache and key in cache:
-        return {int(b): k for b, k in cache[key]["choice"].items()}, cache[key]["report"]
+        return {int(b): tuple(k) for b, k in cache[key]["choice"].items()}, cache[key]["report"]
     by_bucket = {}
     for cell in cells:
         by_bucket.setdefault(bucket_of(cell[0].N), []).append(cell)
@@ -73,14 +86,19 @@ def tune(cells, trials: int, accept_mode: int = 0, sample: int = 48, use_cache: 
         pick = [members[i] for i in rng.choice(len(members), size=min(sample, len(members)), replace=False)]
         rates = {}
         for K in CANDIDATE_K:
-            dt = _time_batch(torch, pick, K, trials, accept_mode)
-            rates[K] = len(pick) * (trials // K) * K / dt
+            for threads in CANDIDATE_THREADS:
+                dt = _time_batch(torch, pick, K, trials, accept_mode, threads)
+                if dt is not None:
+                    rates[(K, threads)] = len(pick) * (trials // K) * K / dt
         best = max(rates, key=rates.get)
+        feasible = sorted({k for k, _ in rates})
         choice[b] = best
         report[str(b)] = {"sites": list(BUCKETS[b]), "cells_sampled": len(pick),
-                          "trials_per_s": {str(k): v for k, v in rates.items()}, "K": best}
+                          "trials_per_s": {f"{k}x{t}": v for (k, t), v in rates.items()},
+                          "K": best[0], "threads": best[1], "K_tested": feasible,
+                          "bracketed": feasible[0] < best[0] < feasible[-1]}
     if use_cache:
-        cache[key] = {"choice": {str(b): k for b, k in choice.items()}, "report": report}
+        cache[key] = {"choice": {str(b): list(k) for b, k in choice.items()}, "report": report}
         try:
             os.makedirs(os.path.dirname(path), exist_ok=True)
             with open(path, "w") as fh:

@@ -16,7 +16,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libhea.so")
 SOURCES = ["hea_api.cu", "hea_counts.cu", "hea_delta.cu", "hea_search_fcc.cu", "hea_search_bcc.cu", "hea_coop_fcc.cu",
-           "hea_coop_bcc.cu", "hea_noalloc.cu", "hea_global.cu", "hea_map.cu"]
+           "hea_coop_bcc.cu", "hea_noalloc.cu", "hea_global.cu", "hea_map.cu", "hea_probe.cu"]
 HEADERS = ["hea_device.cuh", "hea_internal.h", "hea_search.cuh", "hea_coop.cuh", "hea_search_kind.inc"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

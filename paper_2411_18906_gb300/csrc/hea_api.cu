@@ -84,7 +84,8 @@ hea_status check_params(const hea_lattice* lat, const hea_search_params* p) {
     if (p->depth_limit < 0 || p->max_accept < 0 || p->depth0 < 0) return fail(HEA_EINVAL, "negative depth_limit, max_accept or depth0");
     if (p->group_size < 0 || p->group_top < 0) return fail(HEA_EINVAL, "negative group_size or group_top");
     if (!(p->threshold >= 0.0) || !std::isfinite(p->threshold)) return fail(HEA_EINVAL, "threshold must be finite and >= 0");
-    if (p->reserved != 0) return fail(HEA_EINVAL, "reserved field must be 0");
+    if (p->threads != 0 && p->threads != 128 && p->threads != 256 && p->threads != 512)
+        return fail(HEA_EINVAL, "threads = %d must be 0, 128, 256 or 512", p->threads);
     if (p->sync_wait_us < 0) return fail(HEA_EINVAL, "sync_wait_us < 0");
     if (p->test_withhold_cta < 0) return fail(HEA_EINVAL, "test_withhold_cta < 0");
     if (p->timeout_us < 0) return fail(HEA_EINVAL, "timeout_us < 0");
@@ -122,6 +123,7 @@ hea_status place_chain(const hea_lattice* lat, int S, const hea_search_params* p
 
 // Cooperative chain: K = ctas * Kc; multi-accept needs group_size = Kc and 1 <= group_top <= 4.
 hea_status check_coop(const hea_search_params* p, int ctas, int* Kc_out, int* top_out) {
+    if (p->threads != 0) return fail(HEA_EINVAL, "threads must be 0 for a cooperative search (512 threads per CTA)");
     if (ctas < 1 || ctas > 65535) return fail(HEA_EINVAL, "ctas = %d outside [1, 65535]", ctas);
     if (p->K % ctas != 0) return fail(HEA_EINVAL, "K = %d is not a multiple of ctas = %d", p->K, ctas);
     const int Kc = p->K / ctas;
@@ -159,6 +161,7 @@ void fill_params(const hea_search_params* p, hea::ChainDesc* d) {
     d->threshold = p->threshold;
     d->wait_ns = (p->sync_wait_us > 0 ? (int64_t)p->sync_wait_us : 2000000ll) * 1000;
     d->withhold = p->test_withhold_cta;
+    d->threads = p->threads > 0 ? p->threads : hea::kChainThreads;
 }
 
 // Cooperative chain: the chain arrays, the fixed-point tables and the walk over `nrec` merged
@@ -221,13 +224,16 @@ hea_status check_global(const hea_lattice* lat, const hea_objective* obj, const 
     return check_params(lat, sp);
 }
 
-// Plan = header + descriptors sorted by lattice kind (FCC first), then largest work first.
+// Plan = header + descriptors sorted into launch groups by (lattice kind, threads per CTA), each
+// group largest work first.
+constexpr int kThreadChoices = 3;   // 128, 256, 512 threads per CTA
+int thread_group(int threads) { return threads <= 128 ? 0 : (threads <= 256 ? 1 : 2); }
 struct PlanHeader {
     uint64_t magic;
     int32_t n;
-    int32_t n_kind[2];     // cells per lattice kind
-    uint32_t smem_max[2];  // dynamic shared memory per kind
     int32_t pad;
+    int32_t n_group[2][kThreadChoices];     // cells per (kind, threads) group
+    uint32_t smem_max[2][kThreadChoices];   // dynamic shared memory per group
 };
 constexpr uint64_t kPlanMagic = 0x6865615F706C616EULL;  // "hea_plan"
 
@@ -406,14 +412,16 @@ hea_status hea_search_batch_plan(int n, const hea_lattice* const* lats, const he
     // Largest cells first, so that the hardware block scheduler hands the longest chains out first.
     std::stable_sort(descs.begin(), descs.end(), [](const hea::ChainDesc& a, const hea::ChainDesc& b) {
         if (a.kind != b.kind) return a.kind < b.kind;
+        if (a.threads != b.threads) return a.threads < b.threads;
         return (int64_t)a.N * a.K > (int64_t)b.N * b.K;
     });
     PlanHeader h{};
     h.magic = kPlanMagic;
     h.n = n;
     for (const auto& d : descs) {
-        h.n_kind[d.kind] += 1;
-        h.smem_max[d.kind] = std::max(h.smem_max[d.kind], d.smem_bytes);
+        const int g = thread_group(d.threads);
+        h.n_group[d.kind][g] += 1;
+        h.smem_max[d.kind][g] = std::max(h.smem_max[d.kind][g], d.smem_bytes);
     }
     std::memset(plan_host, 0, plan_offset());
     std::memcpy(plan_host, &h, sizeof h);
@@ -428,13 +436,19 @@ hea_status hea_search_batch(const void* plan_host, const void* plan_dev, void* s
     if (h.magic != kPlanMagic || h.n < 1) return fail(HEA_EINVAL, "plan_host is not a plan written by hea_search_batch_plan");
     const hea::ChainDesc* descs = reinterpret_cast<const hea::ChainDesc*>(static_cast<const char*>(plan_dev) + plan_offset());
     cudaStream_t s = as_stream(stream);
-    if (h.n_kind[0] > 0) {
-        hea_status st = cuda_status(hea::launch_search_batch_fcc(descs, h.n_kind[0], h.smem_max[0], s), "hea_search_batch launch");
-        if (st != HEA_OK) return st;
-    }
-    if (h.n_kind[1] > 0)
-        return cuda_status(hea::launch_search_batch_bcc(descs + h.n_kind[0], h.n_kind[1], h.smem_max[1], s),
-                           "hea_search_batch launch");
+    static const int threads_of[kThreadChoices] = {128, 256, 512};
+    int first = 0;
+    for (int kind = 0; kind < 2; ++kind)
+        for (int g = 0; g < kThreadChoices; ++g) {
+            const int cnt = h.n_group[kind][g];
+            if (cnt == 0) continue;
+            const cudaError_t e = (kind == HEA_FCC)
+                                      ? hea::launch_search_batch_fcc(descs + first, cnt, h.smem_max[kind][g], threads_of[g], s)
+                                      : hea::launch_search_batch_bcc(descs + first, cnt, h.smem_max[kind][g], threads_of[g], s);
+            hea_status st = cuda_status(e, "hea_search_batch launch");
+            if (st != HEA_OK) return st;
+            first += cnt;
+        }
     return ok();
 }
 
@@ -486,6 +500,14 @@ hea_status hea_search_coop(const hea_lattice* lat, const hea_objective* obj, con
     const cudaError_t e = (d.kind == HEA_FCC) ? hea::launch_search_coop_fcc(d, as_stream(stream))
                                               : hea::launch_search_coop_bcc(d, as_stream(stream));
     return cuda_status(e, "hea_search_coop launch");
+}
+
+hea_status hea_probe_smem_gather(int mode, int ctas, int64_t iters, uint64_t* sink, void* stream) {
+    if (mode != 0 && mode != 1) return fail(HEA_EINVAL, "mode must be 0 (random) or 1 (one bank per lane)");
+    if (ctas < 1 || ctas > 65535 || iters < 1 || !sink) return fail(HEA_EINVAL, "bad ctas, iters or sink");
+    return cuda_status(hea::launch_smem_gather_probe(mode, ctas, iters, reinterpret_cast<unsigned long long*>(sink),
+                                                     as_stream(stream)),
+                       "hea_probe_smem_gather launch");
 }
 
 hea_status hea_map_structure(const hea_lattice* lat, int64_t n, const double* xyz, const uint8_t* species, int S,
@@ -565,8 +587,8 @@ hea_status hea_global_search(const hea_lattice* lat, const hea_objective* obj, c
         // 4: one refinement chain per slot.
         if (e == cudaSuccess) e = hea::launch_global_descs(d, descs, PL, types, counts, res, N, E, (uint32_t)g * 65536u, s);
         if (e == cudaSuccess)
-            e = (d.kind == HEA_FCC) ? hea::launch_search_batch_fcc(descs, PL, d.smem_bytes, s)
-                                    : hea::launch_search_batch_bcc(descs, PL, d.smem_bytes, s);
+            e = (d.kind == HEA_FCC) ? hea::launch_search_batch_fcc(descs, PL, d.smem_bytes, d.threads, s)
+                                    : hea::launch_search_batch_bcc(descs, PL, d.smem_bytes, d.threads, s);
         // 5: rank the refined set, keep it in rank order at the front of the pool.
         if (e == cudaSuccess) e = hea::launch_global_rank(res, PL, order, lg, result, s);
         if (e == cudaSuccess)

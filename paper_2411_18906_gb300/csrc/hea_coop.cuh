@@ -795,7 +795,8 @@ __device__ void coop_walk(const ChainDesc& d, ChainSmem& m, ChainShared& sh, con
         }
     }
     __syncthreads();
-    if (!sh.n_amb && d.max_accept == 0 && sh.n_edges <= kFastEdges) {
+    // The edge list holds 2 nrec pairs; with more conflicting pairs the full path (conflict matrix) runs.
+    if (!sh.n_amb && d.max_accept == 0 && sh.n_edges <= kFastEdges && sh.n_edges <= 2 * d.nrec) {
         // Fast path: every record is accepted unless it conflicts with an accepted record before it
         // in (D, k) order.  Only the conflicting pairs need an order: one thread per edge orients it
         // (at the precision that settles it), then the greedy choice is the fixed point of

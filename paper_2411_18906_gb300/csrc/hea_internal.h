@@ -8,7 +8,8 @@
 
 namespace hea {
 
-constexpr int kChainThreads = 256;   // threads of a single-CTA search chain
+constexpr int kChainThreads = 256;   // threads of a single-CTA search chain (default)
+constexpr int kChainMaxThreads = 512;
 constexpr int kCoopThreads = 512;    // threads of each CTA of a cooperative chain
 constexpr int kMaxK = 4096;          // candidates per CTA per step (cooperative multi-accept: per chunk)
 constexpr int kGlobalMaxSolutions = 4096;  // global search: largest pool
@@ -42,7 +43,7 @@ struct ChainDesc {
     int32_t withhold;       // cooperative chain, testing aid: 1 + index of a CTA that never publishes (0 = none)
     int32_t nrec;           // cooperative chain: most records merged per step (ctas * records per CTA)
     int32_t chunk;          // cooperative multi-accept: candidates scored per pass (the slice is scored in chunks)
-    int32_t pad3;
+    int32_t threads;        // threads per CTA of the single-CTA and batched chains
 };
 
 // Shared-memory layout of one search CTA (offsets in bytes from the dynamic smem base).
@@ -233,13 +234,17 @@ cudaError_t launch_delta_swap(const ChainDesc& d, const uint8_t* types, const in
                               const int64_t* pairs, int64_t K, double* key, int32_t* dcounts, cudaStream_t stream);
 cudaError_t launch_search_fcc(const ChainDesc& d, cudaStream_t stream);
 cudaError_t launch_search_bcc(const ChainDesc& d, cudaStream_t stream);
-cudaError_t launch_search_batch_fcc(const ChainDesc* descs_dev, int n, uint32_t smem_max, cudaStream_t stream);
-cudaError_t launch_search_batch_bcc(const ChainDesc* descs_dev, int n, uint32_t smem_max, cudaStream_t stream);
+cudaError_t launch_search_batch_fcc(const ChainDesc* descs_dev, int n, uint32_t smem_max, int threads,
+                                    cudaStream_t stream);
+cudaError_t launch_search_batch_bcc(const ChainDesc* descs_dev, int n, uint32_t smem_max, int threads,
+                                    cudaStream_t stream);
 cudaError_t launch_search_coop_fcc(const ChainDesc& d, cudaStream_t stream);
 cudaError_t launch_search_coop_bcc(const ChainDesc& d, cudaStream_t stream);
 cudaError_t launch_map_structure(int kind, int Lx, int Ly, int Lz, int64_t n, const double* xyz, const uint8_t* species,
                                  int S, double a, const double* origin, double tol, uint8_t* types, int32_t* scratch,
                                  int64_t* report, cudaStream_t stream);
+cudaError_t launch_smem_gather_probe(int mode, int ctas, int64_t iters, unsigned long long* sink,
+                                     cudaStream_t stream);
 cudaError_t launch_global_select(const double* pool_f2, int P, int PL, int32_t* order, hea_global_log* log,
                                  cudaStream_t stream);
 cudaError_t launch_global_rank(const hea_search_result* res, int PL, int32_t* order, hea_global_log* log,

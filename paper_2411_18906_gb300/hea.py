@@ -38,7 +38,7 @@ class hea_search_params(ctypes.Structure):
                 ("seed", ctypes.c_uint64), ("chain", ctypes.c_uint32), ("step0", ctypes.c_uint32),
                 ("depth0", ctypes.c_int32), ("group_size", ctypes.c_int32), ("group_top", ctypes.c_int32),
                 ("sync_wait_us", ctypes.c_int32), ("timeout_us", ctypes.c_int64), ("test_withhold_cta", ctypes.c_int32),
-                ("reserved", ctypes.c_int32)]
+                ("threads", ctypes.c_int32)]
 
 
 class hea_search_result(ctypes.Structure):
@@ -104,6 +104,7 @@ def lib():
                                       P, P, sz, P]),
             "hea_search_coop_noalloc": (i32, [P, ctypes.POINTER(hea_objective), ctypes.POINTER(hea_search_params),
                                               i32, P, P, P, P]),
+            "hea_probe_smem_gather": (i32, [i32, i32, i64, P, P]),
             "hea_map_structure": (i32, [P, i64, P, P, i32, ctypes.c_double, P, ctypes.c_double, P, P, P, P]),
             "hea_global_search_workspace_bytes": (sz, [P, ctypes.POINTER(hea_objective),
                                                        ctypes.POINTER(hea_global_params)]),
@@ -213,9 +214,10 @@ def hea_delta_swap(lat, obj, types, counts, pairs, K, key, dcounts=None, stream=
 
 
 def search_params(K, max_steps, accept_mode=0, depth_limit=0, max_accept=0, threshold=0.0, seed=1, chain=0,
-                  step0=0, depth0=0, group_size=0, group_top=0, timeout_us=0, sync_wait_us=0, test_withhold_cta=0):
+                  step0=0, depth0=0, group_size=0, group_top=0, timeout_us=0, sync_wait_us=0, test_withhold_cta=0,
+                  threads=0):
     return hea_search_params(K, accept_mode, max_steps, depth_limit, max_accept, threshold, seed, chain, step0,
-                             depth0, group_size, group_top, sync_wait_us, timeout_us, test_withhold_cta, 0)
+                             depth0, group_size, group_top, sync_wait_us, timeout_us, test_withhold_cta, threads)
 
 
 def hea_search(lat, obj, params, types, counts, result, stream=None):
@@ -311,3 +313,7 @@ def hea_map_structure(lat, n, xyz, species, S, a, origin, tol, types, scratch, r
     o = np.ascontiguousarray(origin, dtype=np.float64)
     _check(lib().hea_map_structure(lat.handle, int(n), _ptr(xyz), _ptr(species), int(S), float(a), _ptr(o),
                                    float(tol), _ptr(types), _ptr(scratch), _ptr(report), _stream(stream)))
+
+
+def hea_probe_smem_gather(mode, ctas, iters, sink, stream=None):
+    _check(lib().hea_probe_smem_gather(int(mode), int(ctas), int(iters), _ptr(sink), _stream(stream)))

@@ -186,3 +186,74 @@ def latency_summary(done: List[Completed]) -> dict:
     return {"requests": len(done), "p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
             "mean_s": float(lat.mean()), "max_s": float(lat.max()), "requests_per_s": len(done) / wall,
             "trials_per_s": trials / wall}
+
+
+def _run_alone(torch, req: Request, lat_cache: dict, coop_ctas: int = 0):
+    """One request on the current stream, device-timed (ms): init, recount, search.  With coop_ctas
+    the search runs as one cooperative chain over that many CTAs (best-of-K only)."""
+    cell = req.cell
+    key = (cell.kind, tuple(cell.L), cell.M)
+    if key not in lat_cache:
+        lat_cache[key] = hea.Lattice(cell.kind, cell.L, cell.M)
+    lat = lat_cache[key]
+    obj = hea.Objective(cell.n_per, cell.weights(), cell.targets())
+    types = torch.empty(cell.N, dtype=torch.uint8, device="cuda")
+    counts = torch.empty((cell.M, cell.S, cell.S), dtype=torch.int32, device="cuda")
+    res = torch.zeros(hea.RESULT_BYTES, dtype=torch.uint8, device="cuda")
+    params = hea.search_params(req.K, max(1, req.max_trials // req.K), accept_mode=req.accept_mode,
+                               depth_limit=req.depth_limit, seed=req.seed)
+    ws = torch.zeros(hea.hea_search_coop_workspace_bytes(coop_ctas), dtype=torch.uint8, device="cuda") \
+        if coop_ctas else None
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    hea.hea_init_config(lat, cell.n_per, cell.seed, types)
+    hea.hea_sro_counts(lat, 1, types, cell.S, counts)
+    if coop_ctas:
+        hea.hea_search_coop(lat, obj, params, coop_ctas, types, counts, res, ws)
+    else:
+        hea.hea_search(lat, obj, params, types, counts, res)
+    e1.record()
+    e1.synchronize()
+    return e0.elapsed_time(e1), hea.decode_results(res.cpu().numpy())[0], types
+
+
+def sequential_baseline(requests: List[Request]) -> dict:
+    """The same requests served one at a time by single chains, first come first served: each
+    request's device time alone, then the FIFO latencies those service times give under the same
+    arrival times."""
+    import torch
+    cache = {}
+    service = []
+    for req in sorted(requests, key=lambda r: r.arrival):
+        ms, _, _ = _run_alone(torch, req, cache)
+        service.append((req.arrival, ms / 1e3))
+    free_at = 0.0
+    lat = []
+    for arrival, s in service:
+        start = max(arrival, free_at)
+        free_at = start + s
+        lat.append(free_at - arrival)
+    lat = np.array(lat)
+    svc = np.array([s for _, s in service])
+    wall = free_at - service[0][0]
+    return {"requests": len(service), "mean_service_s": float(svc.mean()), "p50_s": float(np.percentile(lat, 50)),
+            "p99_s": float(np.percentile(lat, 99)), "requests_per_s": len(service) / wall,
+            "utilisation_at_arrival_rate": float(svc.sum() / (service[-1][0] - service[0][0]))}
+
+
+def coop_vs_single(requests: List[Request], ctas: int = 128) -> dict:
+    """The first 256,000-site request alone: single-CTA chain vs one cooperative chain over `ctas`
+    CTAs (K = 256 splits into ctas slices of K / ctas candidates; identical results)."""
+    import torch
+    req = next((r for r in requests if r.cell.N == 256000), None)
+    if req is None or req.K % ctas != 0:
+        return {"skipped": "no 256k request or K not a multiple of the CTA count"}
+    cache = {}
+    ms1, r1, t1 = _run_alone(torch, req, cache)
+    ms2, r2, t2 = _run_alone(torch, req, cache, coop_ctas=ctas)
+    return {"rid": req.rid, "K": req.K, "single_cta_ms": ms1, "coop_ms": ms2, "coop_ctas": ctas,
+            "identical": bool(torch.equal(t1, t2) and r1["f2"] == r2["f2"] and r1["steps"] == r2["steps"]),
+            "steps": r1["steps"],
+            "note": "with K = 256 each CTA scores 2 candidates per step; the per-step exchange between CTAs "
+                    "then costs more than the scoring it spreads"}

@@ -56,6 +56,20 @@ def test_coop_multi_accept_bit_exact(kind, L, M, S, ctas, Kc, top, steps):
     assert np.array_equal(ts, g[0]) and rs["f2"] == g[2]["f2"]
 
 
+@pytest.mark.parametrize("ctas,Kc,top", [(4, 16, 2), (2, 32, 4), (8, 8, 3), (3, 40, 4)])
+def test_coop_dense_conflicts_few_records(ctas, Kc, top):
+    """FCC 4x4x4 with shells 1-3: the closed neighbourhood of a site covers 43 of the 256 sites, so
+    a handful of published records conflict in more pairs than the fast walk's edge list holds
+    (2 per record); the walk must fall back to the conflict matrix."""
+    spec = workloads.fcc_256()
+    entry = workloads.annealed_targets()["pool_fcc_4sp"][0]
+    n_per = workloads.composition_counts(spec.N, entry["fractions"])
+    target = np.array(entry["alpha"])
+    kw = dict(K=ctas * Kc, max_steps=100, accept_mode=1, group_size=Kc, group_top=top, seed=6)
+    g, o, t, cnt = both(spec.kind, spec.L, spec.M, len(n_per), n_per, spec.weights(), target, 3, ctas, **kw)
+    assert_same(g, o)
+
+
 def test_coop_rejects_bad_splits():
     G.ensure_built()
     lat = hea.Lattice(FCC, (4, 4, 4), 3)

@@ -182,6 +182,15 @@ def test_search_fcc256_full_budget_best_of_32():
     assert g[2]["trials"] == 100000
 
 
+def test_search_bcc16k_full_budget_best_of_256():
+    """BCC 20x20x20, 5 x 3200, shells 1-2, target 0: 39,063 steps at K = 256 (10,000,128 trials)."""
+    spec = workloads.bcc_16k()
+    g, o = run_both(spec.kind, spec.L, spec.M, spec.S, spec.n_per, spec.weights(), spec.targets(), spec.seed, K=256,
+                    max_steps=39063, seed=1)
+    assert_same(g, o)
+    assert g[2]["trials"] == 10_000_128
+
+
 @pytest.mark.parametrize("kind,L,M,S,K,steps,seed", [
     (FCC, (2, 2, 2), 5, 3, 8, 300, 1), (BCC, (2, 2, 2), 5, 2, 16, 300, 2),
     (FCC, (3, 5, 4), 3, 5, 64, 400, 3), (BCC, (5, 5, 5), 4, 6, 100, 300, 4),
@@ -373,3 +382,45 @@ def test_two_bit_species_storage_half_million_sites(mode):
                     accept_mode=mode, seed=4)
     assert_same(g, o)
     assert o[2]["accepted"] > 0
+
+
+# ------------------------------------------------------------------------------------------------
+# Threads per CTA (a launch shape: results must not depend on it)
+# ------------------------------------------------------------------------------------------------
+@pytest.mark.parametrize("threads", [128, 512])
+@pytest.mark.parametrize("kind,L,M,S,K,mode,steps,seed", [
+    (FCC, (4, 4, 4), 3, 4, 32, 0, 400, 1), (BCC, (20, 20, 20), 2, 5, 1024, 0, 60, 2),
+    (FCC, (6, 6, 6), 3, 4, 256, 1, 30, 3), (BCC, (10, 10, 10), 3, 6, 700, 1, 20, 4),
+    (FCC, (3, 3, 3), 5, 3, 64, 1, 60, 5), (BCC, (16, 16, 16), 2, 4, 2048, 1, 3, 6),
+])
+def test_search_threads_per_cta_bit_exact(threads, kind, L, M, S, K, mode, steps, seed):
+    N = oracle.num_sites(kind, L)
+    rng = np.random.default_rng(seed)
+    n_per = composition(N, S, rng)
+    w, target = random_objective(M, S, rng, scale=0.7, symmetric=mode == 1)
+    t = oracle.init_config(N, n_per, seed)
+    cnt = oracle.counts(kind, L, M, S, t)
+    kw = dict(K=K, max_steps=steps, accept_mode=mode, seed=seed + 30)
+    o = oracle.search(kind, L, M, n_per, w, target, t, cnt, **kw)[:3]
+    g = G.gpu_search(kind, L, M, n_per, w, target, t, cnt, threads=threads, **kw)
+    assert_same(g, o)
+
+
+def test_batch_mixed_threads_per_cta():
+    rng = np.random.default_rng(5)
+    cells, params, want = [], [], []
+    for c, (kind, L, M, S, threads) in enumerate([(FCC, (4, 4, 4), 3, 4, 128), (BCC, (6, 5, 4), 2, 3, 512),
+                                                  (FCC, (5, 5, 5), 2, 5, 256), (BCC, (8, 8, 8), 3, 4, 128),
+                                                  (FCC, (3, 4, 5), 3, 6, 512), (BCC, (3, 3, 3), 1, 2, 0)]):
+        N = oracle.num_sites(kind, L)
+        n_per = composition(N, S, rng)
+        w, target = random_objective(M, S, rng, scale=0.5)
+        t = oracle.init_config(N, n_per, 60 + c)
+        cnt = oracle.counts(kind, L, M, S, t)
+        kw = dict(K=int(rng.choice([32, 128, 512])), max_steps=80, accept_mode=c % 2, seed=70 + c, chain=c)
+        cells.append((kind, L, M, n_per, w, target, t, cnt))
+        params.append(dict(kw, threads=threads))
+        want.append(oracle.search(kind, L, M, n_per, w, target, t, cnt, **kw)[:3])
+    ts, cs, rs = G.gpu_search_batch(cells, params)
+    for c in range(len(cells)):
+        assert_same((ts[c], cs[c], rs[c]), want[c])
