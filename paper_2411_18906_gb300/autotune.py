@@ -17,7 +17,7 @@ import numpy as np
 
 from . import hea
 
-CANDIDATE_K = (128, 256, 512, 1024, 2048, 4096)
+CANDIDATE_K = (128, 256, 512, 1024, 2048, 3072, 4096)
 CANDIDATE_THREADS = (128, 256, 512)
 BUCKETS = ((0, 4000), (4000, 12000), (12000, 1 << 30))   # sites
 
