@@ -201,6 +201,22 @@ def measure_smem_gather_peak(torch, hea, sms, iters=4000):
     return out
 
 
+SECONDARY_LEGS = ("single", "recount", "batched", "global", "serve")
+
+
+def secondary_legs(args):
+    """The measurements beside the headline that this run takes (--secondary, --no-secondary)."""
+    if args.no_secondary or args.secondary == "none":
+        return set()
+    if args.secondary == "all":
+        return set(SECONDARY_LEGS)
+    legs = set(x.strip() for x in args.secondary.split(",") if x.strip())
+    unknown = legs - set(SECONDARY_LEGS)
+    if unknown:
+        raise SystemExit(f"unknown secondary legs: {sorted(unknown)}")
+    return legs
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -372,12 +388,18 @@ def run_ours(args):
         "final": {"F": res["f"], "accepted": res["accepted"], "search_steps": res["steps"]},
         "wall_s": wall,
     }
-    if rank == 0 and world == 1 and not args.no_secondary:
-        line["single_chain"] = run_single_chain_configs(torch, hea)
-        line["recount"] = run_recount(torch, hea)
-        line["batched"] = run_batched(torch, hea)
-        line["global_search"] = run_global(torch, hea, table1=not args.no_table1)
-        line["serve"] = run_serving(torch, hea, args.serve_requests)
+    legs = secondary_legs(args)
+    if rank == 0 and world == 1:
+        if "single" in legs:
+            line["single_chain"] = run_single_chain_configs(torch, hea)
+        if "recount" in legs:
+            line["recount"] = run_recount(torch, hea)
+        if "batched" in legs:
+            line["batched"] = run_batched(torch, hea)
+        if "global" in legs:
+            line["global_search"] = run_global(torch, hea, table1=not args.no_table1)
+        if "serve" in legs:
+            line["serve"] = run_serving(torch, hea, args.serve_requests)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args.cpu_steps, ctas, coop_kc, coop_top)
     if rank == 0:
@@ -713,6 +735,8 @@ def main():
                     help="swap trials per step (workload size; the headline workload is 1e8)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-secondary", action="store_true", help="skip every measurement beside the headline")
+    ap.add_argument("--secondary", default="all",
+                    help="measurements beside the headline: all, none, or a comma list of " + ",".join(SECONDARY_LEGS))
     ap.add_argument("--serve-requests", type=int, default=1000,
                     help="requests of the served workload (Poisson, 50/s: 1000 take about 20 s)")
     ap.add_argument("--no-table1", action="store_true", help="skip the Table 1 structures of the global search")
