@@ -393,56 +393,73 @@ static __device__ void carry_winners(ChainSmem& m, const ChainCtx& c, int n) {
 }
 
 // ---- 3./4. exchange -----------------------------------------------------------------------------
-__device__ __forceinline__ void store_release(unsigned long long* p, unsigned long long v) {
-    asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+__device__ __forceinline__ void red_release_add(uint32_t* p, uint32_t v) {
+    asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
-// Waits (each wait bounded by d.wait_ns) for every CTA's tag of local step ls and merges their
-// records into slots [0, sh.qn).  Returns false (in every thread) when a wait ran out.
+__device__ __forceinline__ uint32_t load_acquire_u32(const uint32_t* p) {
+    uint32_t v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Waits (bounded by d.wait_ns) until every CTA has published local step ls, then merges their
+// records into slots [0, sh.qn).  One thread polls the step parity's arrival counter (acquire,
+// with a short sleep between polls so that the grid's pollers leave L2 to the publishers); after
+// the barrier every thread reads one CTA's tag and records from L2 in a single round.  Returns
+// false (in every thread) when the wait ran out.
 static __device__ bool coop_gather(const ChainDesc& d, ChainSmem& m, ChainShared& sh, const ChainCtx& c,
-                                   const unsigned long long* tags, const CoopRecord* recs, int par, uint32_t ls,
-                                   int top) {
+                                   const CoopHeader* hdr, const unsigned long long* tags, const CoopRecord* recs,
+                                   int par, uint32_t ls, int top) {
     const int tid = threadIdx.x, T = blockDim.x, G = gridDim.x;
     if (tid == 0) {
         sh.qn = 0;
         sh.sync_fail = 0;
-    }
-    __syncthreads();
-    for (int r = tid; r < G; r += T) {
-        const unsigned long long* tp = tags + (size_t)par * G + r;
-        unsigned long long t = load_acquire(tp);
-        if ((uint32_t)(t >> 32) != ls + 1u) {
+        const uint32_t target = (uint32_t)G * (ls / 2u + 1u);
+        if (load_acquire_u32(&hdr->arrive[par]) < target) {
             const uint64_t t0 = globaltimer_ns();
             uint32_t it = 0;
-            while ((uint32_t)((t = load_acquire(tp)) >> 32) != ls + 1u) {
-                if ((++it & 31u) == 0u && (int64_t)(globaltimer_ns() - t0) > d.wait_ns) {
+            while (load_acquire_u32(&hdr->arrive[par]) < target) {
+                __nanosleep(64);
+                if ((++it & 15u) == 0u && (int64_t)(globaltimer_ns() - t0) > d.wait_ns) {
                     sh.sync_fail = 1;
                     break;
                 }
             }
         }
-        m.acc[r] = (uint32_t)(t & 0xFFu);
-        if (r == 0) sh.pub_stop = (int)((t >> 16) & 1u);
+        __threadfence();
     }
-    __threadfence();
     __syncthreads();
     if (sh.sync_fail) return false;
     for (int x = tid; x < G * top; x += T) {
         const int r = x / top, i = x - r * top;
-        if (i >= (int)m.acc[r]) continue;
+        const unsigned long long t = __ldcg(tags + (size_t)par * G + r);
         const CoopRecord* R = &recs[((size_t)par * G + r) * kCoopMaxTop + i];
+        // the record's fields are loaded before the tag is checked, so that both take one round trip
+        const double D = __ldcg(&R->D);
+        const float lo = __ldcg(&R->lo), hi = __ldcg(&R->hi);
+        const uint32_t fl = __ldcg(&R->flags), k = __ldcg(&R->k), a = __ldcg(&R->a), b = __ldcg(&R->b);
+        uint64_t g[kMaxShells];
+#pragma unroll
+        for (int s = 0; s < kMaxShells; ++s)
+            if (s < c.M) g[s] = __ldcg(&R->g[s]);
+        if (i == 0 && r == 0) sh.pub_stop = (int)((t >> 16) & 1u);
+        if ((uint32_t)(t >> 32) != ls + 1u) sh.sync_fail = 1;   // cannot happen once the counter is complete
+        if (i >= (int)(t & 0xFFu)) continue;
         const int slot = atomicAdd(&sh.qn, 1);
-        m.qD[slot] = __ldcg(&R->D);
-        m.qlo[slot] = __ldcg(&R->lo);
-        m.qhi[slot] = __ldcg(&R->hi);
-        m.qflag[slot] = __ldcg(&R->flags);
-        m.qk[slot] = __ldcg(&R->k);
-        m.qa[slot] = __ldcg(&R->a);
-        m.qb[slot] = __ldcg(&R->b);
-        for (int k = 0; k < c.M; ++k) m.qg[slot * c.M + k] = __ldcg(&R->g[k]);
+        m.qD[slot] = D;
+        m.qlo[slot] = lo;
+        m.qhi[slot] = hi;
+        m.qflag[slot] = fl;
+        m.qk[slot] = k;
+        m.qa[slot] = a;
+        m.qb[slot] = b;
+#pragma unroll
+        for (int s = 0; s < kMaxShells; ++s)
+            if (s < c.M) m.qg[slot * c.M + s] = g[s];
     }
     __syncthreads();
-    return true;
+    return !sh.sync_fail;
 }
 
 // ---- rank of a list of slots among themselves by (D, k) ------------------------------------------
@@ -1142,6 +1159,10 @@ static __device__ void coop_after_walk(const ChainDesc& d, ChainSmem& m, ChainSh
 template <int KIND, int BITS>
 __device__ void run_coop_chain(const ChainDesc& d, uint8_t* smem, ChainShared& sh) {
     const ChainLayout L = coop_layout(d.N, d.M, d.S, d.qcap, BITS, d.accept_mode, d.nrec);
+    if (L.total > d.smem_bytes) {   // the host placed a different layout: touch nothing
+        if (blockIdx.x == 0) report_invalid(d);
+        return;
+    }
     ChainSmem m(smem, L);
     ChainCtx c;
     chain_setup<KIND, BITS>(d, m, sh, c, false);
@@ -1216,11 +1237,12 @@ __device__ void run_coop_chain(const ChainDesc& d, uint8_t* smem, ChainShared& s
         if (tid == 0 && d.withhold != rank + 1) {
             const unsigned long long stop =
                 (rank == 0 && d.timeout_ns > 0 && (int64_t)(globaltimer_ns() - sh.t0) >= d.timeout_ns) ? 1ull : 0ull;
+            __stcg(&tags[(size_t)par * G + rank], ((unsigned long long)(ls + 1u) << 32) | (stop << 16) |
+                                                      (unsigned long long)n_pub);
             __threadfence();
-            store_release(&tags[(size_t)par * G + rank], ((unsigned long long)(ls + 1u) << 32) | (stop << 16) |
-                                                             (unsigned long long)n_pub);
+            red_release_add(&hdr->arrive[par], 1u);
         }
-        if (!coop_gather(d, m, sh, c, tags, recs, par, ls, top)) {
+        if (!coop_gather(d, m, sh, c, hdr, tags, recs, par, ls, top)) {
             if (tid == 0) {
                 sh.status = HEA_ESYNC;
                 atomicExch(&hdr->error, 1);

@@ -175,12 +175,14 @@ __host__ __device__ inline ChainLayout coop_layout(int N, int M, int S, int qcap
 // Exchange area of a cooperative chain (caller-provided device memory): a header, then for each
 // of two step parities and each CTA a tag word, then for each parity and CTA up to kCoopMaxTop
 // candidate records.  CTA r publishes step s (counted from 0 in each launch) by writing its records
-// and then, with release semantics, the tag ((s + 1) << 32) | (stop << 16) | count; the others
-// read the records once they see that tag (acquire).  Only CTA 0 sets `stop` (time budget spent),
-// so every CTA takes the same stop decision for the same step.
+// and the tag ((s + 1) << 32) | (stop << 16) | count, then adding 1 (release) to the arrival
+// counter of the step's parity.  A CTA reads the records of step s once that counter reaches
+// ctas * (s / 2 + 1) (acquire): one polling thread per CTA on one word.  Only CTA 0 sets `stop`
+// (time budget spent), so every CTA takes the same stop decision for the same step.
 struct CoopHeader {
     int32_t error;              // a wait for another CTA's records ran out
-    int32_t pad[15];
+    uint32_t arrive[2];         // CTAs that published, per step parity (cumulative over the launch)
+    int32_t pad[13];
 };
 
 struct CoopRecord {

@@ -1456,10 +1456,4 @@ __device__ void run_chain(const ChainDesc& d, uint8_t* smem, ChainShared& sh) {
     write_back<BITS>(d, m, sh, c);
 }
 
-__device__ __forceinline__ unsigned long long load_acquire(const unsigned long long* p) {
-    unsigned long long v;
-    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
-    return v;
-}
-
 }  // namespace hea
