@@ -725,13 +725,12 @@ __device__ void coop_walk(const ChainDesc& d, ChainSmem& m, ChainShared& sh, con
         const int A = w.spec[2 * q], B = w.spec[2 * q + 1];
         const uint64_t g_k = m.qg[q * M + k];
         int8_t* row = w.dense + q * Ep + k * SS;
-        // entries visited from a lane-dependent start, so that the lanes' atomics on the per-entry
-        // totals rarely meet on one address
-        for (int t = 0, idx = lane % SS; t < SS; ++t, idx = (idx + 1 == SS) ? 0 : idx + 1) {
-            const int i = idx / S, j = idx - i * S;
-            const int v = entry_delta(g_k, A, B, i, j);
-            row[idx] = (int8_t)v;
-            if (v) atomicAdd(&w.Ptot[k * SS + idx], v < 0 ? -v : v);
+        for (int idx = 0, i = 0, j = 0; idx < SS; ++idx) {
+            row[idx] = (int8_t)entry_delta(g_k, A, B, i, j);
+            if (++j == S) {
+                j = 0;
+                ++i;
+            }
         }
         if (k == M - 1)
             for (int e = E; e < Ep; ++e) w.dense[q * Ep + e] = 0;
@@ -790,6 +789,20 @@ __device__ void coop_walk(const ChainDesc& d, ChainSmem& m, ChainShared& sh, con
             atomicAnd(&w.cellA[hc >> 5], ~(1u << (hc & 31)));
             atomicAnd(&w.cellB[hc >> 5], ~(1u << (hc & 31)));
         }
+        // per-entry totals sum over the records of |dN_e|, in parts of the record list
+        {
+            const int parts = max(1, T / Ep);
+            for (int x = tid; x < Ep * parts; x += T) {
+                const int e = x % Ep, part = x / Ep;
+                int sum = 0;
+                for (int q = part; q < ne; q += parts) {
+                    const int v = w.dense[q * Ep + e];
+                    sum += v < 0 ? -v : v;
+                }
+                if (sum) atomicAdd(&w.Ptot[e], sum);
+            }
+        }
+        __syncthreads();
         for (int q = tid; q < ne; q += T) {
             const int8_t* row = w.dense + q * Ep;
             float U = 0.f, tin = 0.f;
@@ -839,25 +852,31 @@ __device__ void coop_walk(const ChainDesc& d, ChainSmem& m, ChainShared& sh, con
             w.edge[x] = o == 1 ? (((uint32_t)u << 16) | (uint32_t)v) : (((uint32_t)v << 16) | (uint32_t)u);
         }
         __syncthreads();
-        if (tid == 0) {
-            uint32_t* pred = w.accb + nw;   // records with an accepted record before them in a conflict
+        if (warp == 0) {
+            // accepted = all records except those with an accepted record before them in a conflict,
+            // iterated from all-accepted to the fixed point; one lane per edge (ned <= 64), one per word
+            uint32_t* pred = w.accb + nw;
+            uint32_t e0 = 0u, e1 = 0u;
+            const bool h0 = lane < ned, h1 = lane + 32 < ned;
+            if (h0) e0 = w.edge[lane];
+            if (h1) e1 = w.edge[lane + 32];
             for (int sweep = 0; sweep <= ned; ++sweep) {
-                for (int y = 0; y < nw; ++y) pred[y] = 0u;
-                for (int x = 0; x < ned; ++x) {
-                    const int u = (int)(w.edge[x] >> 16), v = (int)(w.edge[x] & 0xFFFFu);
-                    if ((w.accb[u >> 5] >> (u & 31)) & 1u) pred[v >> 5] |= 1u << (v & 31);
-                }
+                if (lane < nw) pred[lane] = 0u;
+                __syncwarp();
+                if (h0 && ((w.accb[e0 >> 21] >> ((e0 >> 16) & 31)) & 1u))
+                    atomicOr(&pred[(e0 & 0xFFFFu) >> 5], 1u << (e0 & 31));
+                if (h1 && ((w.accb[e1 >> 21] >> ((e1 >> 16) & 31)) & 1u))
+                    atomicOr(&pred[(e1 & 0xFFFFu) >> 5], 1u << (e1 & 31));
+                __syncwarp();
                 bool changed = false;
-                for (int x = 0; x < ned; ++x) {
-                    const int v = (int)(w.edge[x] & 0xFFFFu);
-                    const uint32_t bit = 1u << (v & 31);
-                    const bool want = !(pred[v >> 5] & bit), acc = (w.accb[v >> 5] & bit) != 0u;
-                    if (want != acc) {
-                        w.accb[v >> 5] ^= bit;
-                        changed = true;
-                    }
+                if (lane < nw) {
+                    const uint32_t all = (lane == nw - 1 && (ne & 31)) ? ((1u << (ne & 31)) - 1u) : 0xFFFFFFFFu;
+                    const uint32_t nv = all & ~pred[lane];
+                    changed = nv != w.accb[lane];
+                    w.accb[lane] = nv;
                 }
-                if (!changed) break;
+                __syncwarp();
+                if (!__any_sync(0xFFFFFFFFu, changed)) break;
             }
         }
         __syncthreads();
@@ -1013,26 +1032,53 @@ __device__ void coop_walk(const ChainDesc& d, ChainSmem& m, ChainShared& sh, con
                         }
                     }
             }
+            // candidates blocked by earlier batches are never accepted; the cross terms of candidates
+            // that are not (assumed) accepted, included in the prefix sums, are taken out again
+            // wherever a sum spans them
             const uint32_t open = __ballot_sync(0xFFFFFFFFu, lane < nb && prior == 0u);
-            // candidates blocked by earlier batches are never accepted: their cross terms, included in
-            // the prefix sums, are taken out again wherever a sum spans them (rare)
-            const uint32_t blk = __ballot_sync(0xFFFFFFFFu, lane < nb && prior != 0u);
             float cc = 0.f, ce = 0.f;            // corrections from committed accepted candidates
             uint32_t accm = 0u;                  // committed accepted candidates of the batch
             int n_acc = acc_before, nbacc = 0, p = 0;
             bool done = false;
             while (p < nb && !done) {
-                const uint32_t guess = open & ~((1u << p) - 1u);
+                // The guess: the greedy choice among the open candidates from p on if every one of them
+                // were eligible -- accepted unless it conflicts with a committed or an earlier guessed
+                // candidate.  Each lane depends only on earlier lanes, so iterating the rule from
+                // "all open" reaches its unique fixed point (one ballot per link of the longest chain).
+                // Candidates that no choice among the undecided ones before them can make eligible:
+                // their key at its lowest (committed cross terms plus every negative cross term from
+                // p on; sum min(0, X) = (sum X - sum |X|) / 2) is not eligible.  They are rejected
+                // without ending a round.
+                bool srej = false;
+                if (lane >= p && lane < nb && ((open >> lane) & 1u) && !sure && !batch_sure) {
+                    const float se = ce + (pej - PEl[p]);
+                    const float er = fmaf(fmaf(2.0f, se, E0), 1.0f + 256.0f * kTwoUlp,
+                                          fmaf(256.0f * kTwoUlp, fabsf(D0) + 2.0f * (paj + pej), kAbsBound));
+                    const float low = cc + 0.5f * ((pxj - PXl[p]) - (paj - PAl[p]));
+                    const float vmin = fmaf(2.0f, low, D0);
+                    srej = eligible_interval(__fadd_rd(vmin, -2.0f * er), CUDART_INF_F, c.pos_thr, c.thr_lo,
+                                             c.thr_hi) == 0;
+                }
+                const uint32_t cand = open & ~((1u << p) - 1u) & ~__ballot_sync(0xFFFFFFFFu, srej);
+                uint32_t guess = cand;
+                for (int it = 0; it <= 32; ++it) {
+                    const bool in = ((cand >> lane) & 1u) && (mask & (accm | guess)) == 0u;
+                    const uint32_t ng = __ballot_sync(0xFFFFFFFFu, in);
+                    if (ng == guess) break;
+                    guess = ng;
+                }
+                // A guessed candidate is decided against the committed ones and the guessed ones before
+                // it; a candidate left out of the guess is rejected by the guessed one it conflicts with.
+                // The round ends at the first guessed candidate that is not eligible (or open).
                 int dec = 0;
-                if (lane >= p && lane < nb) {
+                if (lane >= p && lane < nb && ((guess >> lane) & 1u)) {
                     const uint32_t gl = guess & ((1u << lane) - 1u);
-                    const bool blocked = prior != 0u || (mask & (accm | gl)) != 0u;
-                    if (!blocked) {
+                    {
                         if (sure || (acc_before == 0 && (accm | gl) == 0u)) {
                             dec = 1;   // sure, or the step-start state: the candidate is eligible
                         } else {
                             float sx = cc + (pxj - PXl[p]);
-                            for (uint32_t bb = blk & gl_span(p, lane); bb; bb &= bb - 1u) sx -= XTl[__ffs(bb) - 1];
+                            for (uint32_t bb = ~guess & gl_span(p, lane); bb; bb &= bb - 1u) sx -= XTl[__ffs(bb) - 1];
                             const float se = ce + (pej - PEl[p]);
                             const float v = fmaf(2.0f, sx, D0);
                             // Rounding: every prefix sum (5 additions), difference and fold (at most 32
@@ -1044,7 +1090,7 @@ __device__ void coop_walk(const ChainDesc& d, ChainSmem& m, ChainShared& sh, con
                         }
                     }
                 }
-                const uint32_t bad = __ballot_sync(0xFFFFFFFFu, lane >= p && lane < nb && prior == 0u && dec != 1);
+                const uint32_t bad = __ballot_sync(0xFFFFFFFFu, lane >= p && lane < nb && ((guess >> lane) & 1u) && dec != 1);
                 const int js = bad ? (__ffs(bad) - 1) : nb;
                 uint32_t commit = guess & ((js >= 32) ? 0xFFFFFFFFu : ((1u << js) - 1u));
                 if (d.max_accept > 0) {
@@ -1054,12 +1100,12 @@ __device__ void coop_walk(const ChainDesc& d, ChainSmem& m, ChainShared& sh, con
                     if (__popc(all) > room) done = true;
                 }
                 if (commit) {
-                    // commit is the open candidates of [p, end): fold their cross terms in
+                    // commit is the guessed candidates of [p, end): fold their cross terms in
                     const int end = 32 - __clz(commit);   // one past the last committed candidate
                     if (lane >= end && lane < nb) {
                         cc += PXl[end] - PXl[p];
                         ce += PEl[end] - PEl[p];
-                        for (uint32_t bb = blk & gl_span(p, end); bb; bb &= bb - 1u) cc -= XTl[__ffs(bb) - 1];
+                        for (uint32_t bb = ~commit & gl_span(p, end); bb; bb &= bb - 1u) cc -= XTl[__ffs(bb) - 1];
                     }
                 }
                 if (lane == 0)
