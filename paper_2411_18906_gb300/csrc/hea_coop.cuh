@@ -739,17 +739,40 @@ __device__ void coop_walk(const ChainDesc& d, ChainSmem& m, ChainShared& sh, con
         const int16_t* P3 = w.pos + 3 * s2;
         const int cx = P3[0] >> 1, cy = P3[1] >> 1, cz = P3[2] >> 1;
         bool near = false;
-        for (int dz = -rc; dz <= rc && !near; ++dz)
-            for (int dy = -rc; dy <= rc && !near; ++dy)
-                for (int dx = -rc; dx <= rc; ++dx) {
-                    const uint32_t hc = cell_hash(c.g, wrap_cell(cx + dx, c.g.Lx), wrap_cell(cy + dy, c.g.Ly),
-                                                  wrap_cell(cz + dz, c.g.Lz));
-                    const uint32_t* map = (dx == 0 && dy == 0 && dz == 0) ? w.cellB : w.cellA;
-                    if ((map[hc >> 5] >> (hc & 31)) & 1u) {
-                        near = true;
-                        break;
+        if (rc == 1) {
+            // the 27 cells at once (independent loads)
+            int wx[3], wy[3], wz[3];
+#pragma unroll
+            for (int o = 0; o < 3; ++o) {
+                wx[o] = wrap_cell(cx + o - 1, c.g.Lx);
+                wy[o] = wrap_cell(cy + o - 1, c.g.Ly);
+                wz[o] = wrap_cell(cz + o - 1, c.g.Lz);
+            }
+            uint32_t hit = 0u;
+#pragma unroll
+            for (int oz = 0; oz < 3; ++oz)
+#pragma unroll
+                for (int oy = 0; oy < 3; ++oy)
+#pragma unroll
+                    for (int ox = 0; ox < 3; ++ox) {
+                        const uint32_t hc = cell_hash(c.g, wx[ox], wy[oy], wz[oz]);
+                        const uint32_t* map = (ox == 1 && oy == 1 && oz == 1) ? w.cellB : w.cellA;
+                        hit |= (map[hc >> 5] >> (hc & 31)) & 1u;
                     }
-                }
+            near = hit != 0u;
+        } else {
+            for (int dz = -rc; dz <= rc && !near; ++dz)
+                for (int dy = -rc; dy <= rc && !near; ++dy)
+                    for (int dx = -rc; dx <= rc; ++dx) {
+                        const uint32_t hc = cell_hash(c.g, wrap_cell(cx + dx, c.g.Lx), wrap_cell(cy + dy, c.g.Ly),
+                                                      wrap_cell(cz + dz, c.g.Lz));
+                        const uint32_t* map = (dx == 0 && dy == 0 && dz == 0) ? w.cellB : w.cellA;
+                        if ((map[hc >> 5] >> (hc & 31)) & 1u) {
+                            near = true;
+                            break;
+                        }
+                    }
+        }
         if (near) w.susp[atomicAdd(&sh.n_pairs, 1)] = (uint16_t)s2;
     }
     __syncthreads();
@@ -803,25 +826,36 @@ __device__ void coop_walk(const ChainDesc& d, ChainSmem& m, ChainShared& sh, con
             }
         }
         __syncthreads();
-        for (int q = tid; q < ne; q += T) {
-            const int8_t* row = w.dense + q * Ep;
+        // eight lanes per record, each summing every eighth entry (an entry with dN = 0 adds an exact
+        // 0), then a three-level tree: at most 9 roundings per sum, inside the 32 u allowed below
+        for (int q0 = 0; q0 < ne; q0 += T / 8) {
+            const int q = q0 + (tid >> 3), l8 = tid & 7;
             float U = 0.f, tin = 0.f;
-            for (int e = 0; e < E; ++e) {
-                const int dl = row[e];
-                if (dl == 0) continue;
-                const float ad = (float)(dl < 0 ? -dl : dl);
-                U = fmaf(fabsf(m.fa[e]) * ad, (float)w.Ptot[e], U);
-                tin = fmaf(ad, 2.0f * m.tiny[e], tin);
+            if (q < ne) {
+                const int8_t* row = w.dense + q * Ep;
+                for (int e = l8; e < E; e += 8) {
+                    const int dl = row[e];
+                    const float ad = (float)(dl < 0 ? -dl : dl);
+                    U = fmaf(fabsf(m.fa[e]) * ad, (float)w.Ptot[e], U);
+                    tin = fmaf(ad, 2.0f * m.tiny[e], tin);
+                }
             }
-            U = 2.0f * U * (1.0f + 16.0f * kTwoUlp);
-            const float hi = m.qhi[q], lo = m.qlo[q];
-            const float slack = fmaf(kTwoPow20, (hi - lo) + U, tin + kAbsBound);
-            const float top = __fadd_ru(__fadd_ru(hi, U), slack);
-            const bool sure = c.pos_thr ? (top <= c.thr_lo) : (top < 0.f);
-            if (sure)
-                m.qflag[q] |= 64u;
-            else
-                sh.n_amb = 1;
+#pragma unroll
+            for (int o = 4; o > 0; o >>= 1) {
+                U += __shfl_xor_sync(0xFFFFFFFFu, U, o);
+                tin += __shfl_xor_sync(0xFFFFFFFFu, tin, o);
+            }
+            if (q < ne && l8 == 0) {
+                U = 2.0f * U * (1.0f + 16.0f * kTwoUlp);
+                const float hi = m.qhi[q], lo = m.qlo[q];
+                const float slack = fmaf(kTwoPow20, (hi - lo) + U, tin + kAbsBound);
+                const float top = __fadd_ru(__fadd_ru(hi, U), slack);
+                const bool sure = c.pos_thr ? (top <= c.thr_lo) : (top < 0.f);
+                if (sure)
+                    m.qflag[q] |= 64u;
+                else
+                    sh.n_amb = 1;
+            }
         }
     }
     __syncthreads();
