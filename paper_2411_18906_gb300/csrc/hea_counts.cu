@@ -264,51 +264,186 @@ __device__ __forceinline__ W rot_row(W w, int s, int Lx, W mask) {
 __device__ __forceinline__ int popc_w(uint32_t w) { return __popc(w); }
 __device__ __forceinline__ int popc_w(uint64_t w) { return __popcll(w); }
 
+// Half of a centrosymmetric shell: the vectors that are lexicographically positive.
+__device__ __forceinline__ bool half_vector(const signed char* v) {
+    return v[0] > 0 || (v[0] == 0 && (v[1] > 0 || (v[1] == 0 && v[2] > 0)));
+}
+
+// Target row and x shift of shell vector V from row (b, cz, cy).
+template <int KIND>
+__device__ __forceinline__ int vector_row(const signed char* V, int b, int cz, int cy, int Ly, int Lz, int& dcx) {
+    int ox, oy, oz;
+    if (KIND == kFCC) {
+        ox = b >> 1;
+        oy = b & 1;
+        oz = ox ^ oy;
+    } else {
+        ox = oy = oz = b;
+    }
+    const int hx = ox + V[0], hy = oy + V[1], hzz = oz + V[2];
+    dcx = hx >> 1;   // floor division by 2
+    const int dcy = hy >> 1, dcz = hzz >> 1;
+    const int px = hx & 1, py = hy & 1;
+    const int b2 = (KIND == kFCC) ? 2 * px + py : px;
+    int cy2 = cy + dcy, cz2 = cz + dcz;
+    cy2 += (cy2 < 0) ? Ly : 0;
+    cy2 -= (cy2 >= Ly) ? Ly : 0;
+    cz2 += (cz2 < 0) ? Lz : 0;
+    cz2 -= (cz2 >= Lz) ? Lz : 0;
+    return (b2 * Lz + cz2) * Ly + cy2;
+}
+
+// One configuration per CTA.  With every species in [0, S), only the pairs of the first S - 1
+// species are counted, over half of each shell's vectors: the vector -v counts (j, i) where v
+// counts (i, j), so N_ij = sum over the half of c_ij + c_ji; every row of N^(k) sums to
+// N_i Z_k, which gives the pairs with the last species.  A configuration holding any other value
+// counts every pair over every vector (values >= S are then not counted).
 template <int KIND, int S, typename W>
 __global__ void __launch_bounds__(kCountThreads) counts_planes_kernel(Geo g, int M, const uint8_t* __restrict__ types,
                                                                       int32_t* __restrict__ counts) {
     extern __shared__ __align__(16) uint8_t planes_raw[];
+    __shared__ int invalid;
     W* planes = reinterpret_cast<W*>(planes_raw);   // [S][R], one word per row (rows of at most 8 sizeof(W) cells)
     constexpr int B = KIND == kFCC ? 4 : 2;
     constexpr int NP = S * (S + 1) / 2;
+    constexpr int SM1 = S - 1, NSYM = SM1 * (SM1 + 1) / 2;
     const int Lx = g.Lx, Ly = g.Ly, Lz = g.Lz, R = B * Ly * Lz, E = M * S * S;
     const uint8_t* t = types + (size_t)blockIdx.x * (size_t)g.N;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
     const W mask = (Lx == 8 * (int)sizeof(W)) ? ~W(0) : (W)((W(1) << Lx) - W(1));
-    int32_t* wh = reinterpret_cast<int32_t*>(planes + (size_t)S * R);   // [nwarp][E]
-    for (int i = threadIdx.x; i < nwarp * E; i += blockDim.x) wh[i] = 0;
-    // bit planes: one warp per row, two halves of 32 cells
-    for (int r = warp; r < R; r += nwarp) {
-        const uint8_t* row = t + (size_t)r * Lx;   // rows are x-contiguous: ((b Lz + cz) Ly + cy) Lx
-        const int y0 = lane < Lx ? row[lane] : 0xFF;
-        const int y1 = lane + 32 < Lx ? row[lane + 32] : 0xFF;
+    int32_t* wh = reinterpret_cast<int32_t*>(planes + (size_t)S * R);   // [nwarp][E], then [nwarp][S]
+    int32_t* wn = wh + nwarp * E;
+    for (int i = threadIdx.x; i < nwarp * (E + S); i += blockDim.x) wh[i] = 0;
+    if (threadIdx.x == 0) invalid = 0;
+    __syncthreads();
+    // bit planes: one warp per row, two halves of 32 cells; each warp loads 8 rows before it
+    // builds their planes, so that 8 row loads are in flight at once
+    constexpr int RU = 8;
+    bool bad = false;
+    for (int r0 = warp * RU; r0 < R; r0 += nwarp * RU) {
+        int y0[RU], y1[RU];
 #pragma unroll
-        for (int y = 0; y < S; ++y) {
-            const uint32_t lo = __ballot_sync(0xFFFFFFFFu, y0 == y), hi = __ballot_sync(0xFFFFFFFFu, y1 == y);
-            if (lane == 0) planes[(size_t)y * R + r] = (W)((uint64_t)lo | ((uint64_t)hi << 32));
+        for (int u = 0; u < RU; ++u) {
+            const int r = r0 + u;
+            const uint8_t* row = t + (size_t)r * Lx;   // rows are x-contiguous: ((b Lz + cz) Ly + cy) Lx
+            y0[u] = (r < R && lane < Lx) ? row[lane] : 0;
+            y1[u] = (r < R && lane + 32 < Lx) ? row[lane + 32] : 0;
+        }
+#pragma unroll
+        for (int u = 0; u < RU; ++u) {
+            const int r = r0 + u;
+            if (r >= R) break;   // warp-uniform
+            bad = bad || (lane < Lx && y0[u] >= S) || (lane + 32 < Lx && y1[u] >= S);
+#pragma unroll
+            for (int y = 0; y < S; ++y) {
+                const uint32_t lo = __ballot_sync(0xFFFFFFFFu, lane < Lx && y0[u] == y),
+                               hi = __ballot_sync(0xFFFFFFFFu, lane + 32 < Lx && y1[u] == y);
+                if (lane == 0) planes[(size_t)y * R + r] = (W)((uint64_t)lo | ((uint64_t)hi << 32));
+            }
         }
     }
+    if (bad) invalid = 1;
     __syncthreads();
     const ShellTable& TAB = c_shells[KIND];
     const Divider dLy = make_divider((uint32_t)Ly), dLz = make_divider((uint32_t)Lz);
+    auto row_of = [&](int r, int& b, int& cz, int& cy) {
+        const uint32_t t2 = divide((uint32_t)r, dLy);
+        cy = r - (int)t2 * Ly;
+        b = (int)divide(t2, dLz);
+        cz = (int)t2 - b * Lz;
+    };
+    if (!invalid) {
+        int ni[S];
+#pragma unroll
+        for (int a = 0; a < S; ++a) ni[a] = 0;
+        for (int k = 0; k < M; ++k) {
+            int sym[NSYM];
+#pragma unroll
+            for (int x = 0; x < NSYM; ++x) sym[x] = 0;
+            for (int r = threadIdx.x; r < R; r += blockDim.x) {
+                int b, cz, cy;
+                row_of(r, b, cz, cy);
+                W own[SM1];
+#pragma unroll
+                for (int a = 0; a < SM1; ++a) own[a] = planes[(size_t)a * R + r];
+                if (k == 0) {
+#pragma unroll
+                    for (int a = 0; a < SM1; ++a) ni[a] += popc_w(own[a]);
+                    ni[SM1] += popc_w(planes[(size_t)SM1 * R + r]);
+                }
+                for (int v = TAB.first[k]; v < TAB.first[k + 1]; ++v) {
+                    if (!half_vector(TAB.v[v])) continue;
+                    int dcx;
+                    const int r2 = vector_row<KIND>(TAB.v[v], b, cz, cy, Ly, Lz, dcx);
+                    W nb[SM1];
+#pragma unroll
+                    for (int y = 0; y < SM1; ++y) nb[y] = rot_row<W>(planes[(size_t)y * R + r2], dcx, Lx, mask);
+                    int x = 0;
+#pragma unroll
+                    for (int a = 0; a < SM1; ++a) {
+                        sym[x++] += 2 * popc_w((W)(own[a] & nb[a]));
+#pragma unroll
+                        for (int y = a + 1; y < SM1; ++y) sym[x++] += popc_w((W)(own[a] & nb[y])) + popc_w((W)(own[y] & nb[a]));
+                    }
+                }
+            }
+            int x = 0;
+#pragma unroll
+            for (int a = 0; a < SM1; ++a)
+#pragma unroll
+                for (int y = a; y < SM1; ++y) {
+                    const unsigned sum = __reduce_add_sync(0xFFFFFFFFu, (unsigned)sym[x++]);
+                    if (lane == 0) wh[warp * E + (k * S + a) * S + y] = (int)sum;
+                }
+        }
+#pragma unroll
+        for (int a = 0; a < S; ++a) {
+            const unsigned sum = __reduce_add_sync(0xFFFFFFFFu, (unsigned)ni[a]);
+            if (lane == 0) wn[warp * S + a] = (int)sum;
+        }
+        __syncthreads();
+        int32_t* out = counts + (size_t)blockIdx.x * (size_t)E;
+        for (int k = threadIdx.x; k < M; k += blockDim.x) {
+            int nt[S], n[S][S];
+#pragma unroll
+            for (int a = 0; a < S; ++a) {
+                nt[a] = 0;
+                for (int w = 0; w < nwarp; ++w) nt[a] += wn[w * S + a];
+            }
+#pragma unroll
+            for (int a = 0; a < SM1; ++a)
+#pragma unroll
+                for (int y = a; y < SM1; ++y) {
+                    int sum = 0;
+                    for (int w = 0; w < nwarp; ++w) sum += wh[w * E + (k * S + a) * S + y];
+                    n[a][y] = sum;
+                    n[y][a] = sum;
+                }
+            const int Z = TAB.z[k];
+            int last = nt[SM1] * Z;
+#pragma unroll
+            for (int a = 0; a < SM1; ++a) {
+                int rest = nt[a] * Z;
+#pragma unroll
+                for (int y = 0; y < SM1; ++y) rest -= n[a][y];
+                n[a][SM1] = rest;
+                n[SM1][a] = rest;
+                last -= rest;
+            }
+            n[SM1][SM1] = last;
+#pragma unroll
+            for (int a = 0; a < S; ++a)
+#pragma unroll
+                for (int y = 0; y < S; ++y) out[(k * S + a) * S + y] = n[a][y];
+        }
+        return;
+    }
+    // some value outside [0, S): every vector, every pair i <= j of valid species
     for (int base = warp * 32; base < R; base += blockDim.x) {
         const int r = base + lane;
         const bool act = r < R;
         int b = 0, cz = 0, cy = 0;
-        if (act) {
-            const uint32_t t2 = divide((uint32_t)r, dLy);
-            cy = r - (int)t2 * Ly;
-            b = (int)divide(t2, dLz);
-            cz = (int)t2 - b * Lz;
-        }
-        int ox, oy, oz;
-        if (KIND == kFCC) {
-            ox = b >> 1;
-            oy = b & 1;
-            oz = ox ^ oy;
-        } else {
-            ox = oy = oz = b;
-        }
+        if (act) row_of(r, b, cz, cy);
         W own[S];
 #pragma unroll
         for (int a = 0; a < S; ++a) own[a] = act ? planes[(size_t)a * R + r] : W(0);
@@ -317,17 +452,8 @@ __global__ void __launch_bounds__(kCountThreads) counts_planes_kernel(Geo g, int
 #pragma unroll
             for (int x = 0; x < NP; ++x) acc[x] = 0;
             for (int v = TAB.first[k]; v < TAB.first[k + 1]; ++v) {
-                // neighbour offsets in half units -> sublattice and cell offsets of the target row
-                const int hx = ox + TAB.v[v][0], hy = oy + TAB.v[v][1], hzz = oz + TAB.v[v][2];
-                const int dcx = hx >> 1, dcy = hy >> 1, dcz = hzz >> 1;   // floor division by 2
-                const int px = hx & 1, py = hy & 1;
-                const int b2 = (KIND == kFCC) ? 2 * px + py : px;
-                int cy2 = cy + dcy, cz2 = cz + dcz;
-                cy2 += (cy2 < 0) ? Ly : 0;
-                cy2 -= (cy2 >= Ly) ? Ly : 0;
-                cz2 += (cz2 < 0) ? Lz : 0;
-                cz2 -= (cz2 >= Lz) ? Lz : 0;
-                const int r2 = (b2 * Lz + cz2) * Ly + cy2;
+                int dcx = 0;
+                const int r2 = act ? vector_row<KIND>(TAB.v[v], b, cz, cy, Ly, Lz, dcx) : 0;
                 W nb[S];
 #pragma unroll
                 for (int y = 0; y < S; ++y) nb[y] = act ? rot_row<W>(planes[(size_t)y * R + r2], dcx, Lx, mask) : W(0);
@@ -404,7 +530,7 @@ template <int KIND, int S, typename W>
 static cudaError_t launch_planes_w(const Geo& g, int M, int n_configs, const uint8_t* types, int32_t* counts,
                                    cudaStream_t stream) {
     constexpr int B = KIND == kFCC ? 4 : 2;
-    const size_t smem = sizeof(W) * S * B * g.Ly * g.Lz + sizeof(int32_t) * (kCountThreads / 32) * M * S * S;
+    const size_t smem = sizeof(W) * S * B * g.Ly * g.Lz + sizeof(int32_t) * (kCountThreads / 32) * (M * S * S + S);
     cudaError_t err = cudaFuncSetAttribute(counts_planes_kernel<KIND, S, W>,
                                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) {
@@ -426,7 +552,7 @@ static cudaError_t launch_planes_t(const Geo& g, int M, int n_configs, const uin
 static size_t planes_smem(int kind, int Lx, int Ly, int Lz, int M, int S) {
     if (Lx > 64 || S < 2 || S > 6) return 0;
     const int B = kind == kFCC ? 4 : 2;
-    const size_t smem = sizeof(uint64_t) * S * B * Ly * Lz + sizeof(int32_t) * (kCountThreads / 32) * M * S * S;
+    const size_t smem = sizeof(uint64_t) * S * B * Ly * Lz + sizeof(int32_t) * (kCountThreads / 32) * (M * S * S + S);
     return smem <= 200 * 1024 ? smem : 0;
 }
 
