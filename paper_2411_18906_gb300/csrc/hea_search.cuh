@@ -337,6 +337,7 @@ struct ChainCtx {
     float rel;   // (E + 4) 2^-23: relative part of the FP32 key bound
     int qcap;    // candidate slots in shared memory
     int r2max;   // |d|^2 of shell M, half units^2
+    bool alias;  // some axis has at most reach(M) + 1 cells: two shell vectors may reach the same site
     bool pos_thr;            // threshold > 0
     float thr_lo, thr_hi;    // binary32 neighbours of the threshold
 };
@@ -357,6 +358,7 @@ __device__ void chain_setup(const ChainDesc& d, ChainSmem& m, ChainShared& sh, C
     c.rel = (float)(c.E + 4) * kTwoUlp;
     c.qcap = d.qcap;
     c.r2max = c_shells[KIND].radius2[d.M - 1];
+    c.alias = min(d.Lx, min(d.Ly, d.Lz)) <= c_shells[KIND].reach[d.M - 1] + 1;
     c.pos_thr = d.threshold > 0.0;
     {
         float f = (float)d.threshold;
@@ -480,41 +482,74 @@ __device__ float score_range(const ChainDesc& d, ChainSmem& m, ChainShared& sh, 
         // Histograms of both sites.  b can be a shell neighbour of a only when their minimum-image
         // squared distance is at most r2 of shell M; otherwise no neighbour needs skipping.  With at
         // most four species the 8-bit fields fit one 32-bit word.
+        // Outside small cells a shell vector from a reaches b only when it equals their minimum-image
+        // displacement, so a near pair is handled by taking the partner's species out of the one
+        // shell whose radius is their distance; this keeps every candidate on one code path (a lane
+        // on a separate path stalls its warp and fetches cold code).  Small cells (two vectors may
+        // reach the same site) skip every vector that reaches the partner.
         int Xa, Ya, Za, Xb, Yb, Zb;
         site_coords<KIND>(c.g, a, Xa, Ya, Za);
         site_coords<KIND>(c.g, b, Xb, Yb, Zb);
-        const bool near = min_image_r2(Xb - Xa, Yb - Ya, Zb - Za, c.g) <= c.r2max;
+        const int r2ab = min_image_r2(Xb - Xa, Yb - Ya, Zb - Za, c.g);
+        const bool near = r2ab <= c.r2max;
+        const bool skip = near && c.alias;
         uint64_t gb[MX];
         if (c.S <= 4) {
             auto onehot32 = [&](uint32_t n) -> uint32_t { return 1u << (8 * load_species<BITS>(m.types, n)); };
             uint32_t ha[MX], hb[MX];
-            if (near) {
+            if (skip) {
                 neighbour_histogram_at<KIND, MX, true, uint32_t>(c.g, Xa, Ya, Za, b, onehot32, ha, M);
                 neighbour_histogram_at<KIND, MX, true, uint32_t>(c.g, Xb, Yb, Zb, a, onehot32, hb, M);
             } else {
                 neighbour_histogram_at<KIND, MX, false, uint32_t>(c.g, Xa, Ya, Za, 0u, onehot32, ha, M);
                 neighbour_histogram_at<KIND, MX, false, uint32_t>(c.g, Xb, Yb, Zb, 0u, onehot32, hb, M);
+                if (near) {
+#pragma unroll
+                    for (int k = 0; k < MX; ++k)
+                        if (k < M && c_shells[KIND].radius2[k] == r2ab) {
+                            ha[k] -= 1u << (8 * B);
+                            hb[k] -= 1u << (8 * A);
+                        }
+                }
             }
 #pragma unroll
             for (int k = 0; k < MX; ++k) gb[k] = pack_g(ha[k], hb[k]);
         } else {
             uint64_t ha[MX], hb[MX];
-            if (near) {
+            if (skip) {
                 neighbour_histogram_at<KIND, MX, true, uint64_t>(c.g, Xa, Ya, Za, b, onehot, ha, M);
                 neighbour_histogram_at<KIND, MX, true, uint64_t>(c.g, Xb, Yb, Zb, a, onehot, hb, M);
             } else {
                 neighbour_histogram_at<KIND, MX, false, uint64_t>(c.g, Xa, Ya, Za, 0u, onehot, ha, M);
                 neighbour_histogram_at<KIND, MX, false, uint64_t>(c.g, Xb, Yb, Zb, 0u, onehot, hb, M);
+                if (near) {
+#pragma unroll
+                    for (int k = 0; k < MX; ++k)
+                        if (k < M && c_shells[KIND].radius2[k] == r2ab) {
+                            ha[k] -= 1ull << (8 * B);
+                            hb[k] -= 1ull << (8 * A);
+                        }
+                }
             }
 #pragma unroll
             for (int k = 0; k < MX; ++k) gb[k] = pack_g(ha[k], hb[k]);
         }
         float lo = -CUDART_INF_F, hi = CUDART_INF_F;
         if (c.use_filter) {
-            float Dt, err;
-            score_float(M, c.S, m.fa, m.fb, A, B, gb, c.rel, Dt, err);
-            hi = __fadd_ru(Dt, err);
-            lo = __fadd_rd(Dt, -err);
+            // g = 0 in every shell (the two sites see the same species counts): no count changes,
+            // and the key is exactly 0 (the binary64 chain skips every entry)
+            bool zero = true;
+#pragma unroll
+            for (int k = 0; k < MX; ++k) zero = zero && (k >= M || gb[k] == kGBias);
+            if (zero) {
+                lo = 0.f;
+                hi = 0.f;
+            } else {
+                float Dt, err;
+                score_float(M, c.S, m.fa, m.fb, A, B, gb, c.rel, Dt, err);
+                hi = __fadd_ru(Dt, err);
+                lo = __fadd_rd(Dt, -err);
+            }
             my_umin = fminf(my_umin, hi);
             if (c.pos_thr ? (lo > c.thr_hi) : (lo >= 0.f)) continue;   // cannot be accepted
         }

@@ -78,3 +78,30 @@ def test_methods_agree_and_refuse_inapplicable():
     assert e.value.status == hea.HEA_EINVAL
     with pytest.raises(hea.HeaError):
         hea.hea_sro_counts_method(lat, 1, buf, 4, cnt, 3)
+
+
+@pytest.mark.parametrize("method", [1, 2])
+@pytest.mark.parametrize("kind,L,M,S", [(FCC, (3, 3, 3), 2, 3), (BCC, (6, 5, 4), 3, 5)])
+def test_out_of_range_species_not_counted(kind, L, M, S, method):
+    """Sites holding a value >= S drop out of every pair, in both kernels (the bit-plane kernel
+    then counts every pair instead of taking the last species from the row sums)."""
+    N = oracle.num_sites(kind, L)
+    rng = np.random.default_rng(5 * S + M)
+    t = oracle.init_config(N, composition(N, S, rng), 3)
+    t2 = t.copy()
+    t2[::7] = 200                                   # not a species
+    nbr = oracle.neighbours(kind, L, M)
+    Z, _, _ = oracle.shells(kind, M)
+    want = np.zeros((M, S, S), np.int64)
+    for s in range(N):
+        if t2[s] >= S:
+            continue
+        start = 0
+        for k in range(M):
+            for n in nbr[s, start:start + Z[k]]:
+                if t2[n] < S:
+                    want[k, t2[s], t2[n]] += 1
+            start += Z[k]
+    got = run_method(kind, L, M, S, np.stack([t2, t]), method)
+    assert np.array_equal(got[0], want)
+    assert np.array_equal(got[1], oracle.counts(kind, L, M, S, t))
