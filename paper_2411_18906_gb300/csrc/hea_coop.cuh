@@ -427,7 +427,7 @@ static __device__ bool coop_gather(const ChainDesc& d, ChainSmem& m, ChainShared
                 }
             }
         }
-        __threadfence();
+        // the acquire load orders the reads below (through the barrier) after every release it saw
     }
     __syncthreads();
     if (sh.sync_fail) return false;
@@ -1319,7 +1319,8 @@ __device__ void run_coop_chain(const ChainDesc& d, uint8_t* smem, ChainShared& s
                 (rank == 0 && d.timeout_ns > 0 && (int64_t)(globaltimer_ns() - sh.t0) >= d.timeout_ns) ? 1ull : 0ull;
             __stcg(&tags[(size_t)par * G + rank], ((unsigned long long)(ls + 1u) << 32) | (stop << 16) |
                                                       (unsigned long long)n_pub);
-            __threadfence();
+            // release: the records and the tag (written before the barrier above, or by this thread)
+            // are visible to every CTA that acquires the counter value this add produces
             red_release_add(&hdr->arrive[par], 1u);
         }
         if (!coop_gather(d, m, sh, c, hdr, tags, recs, par, ls, top)) {
