@@ -29,21 +29,93 @@ __device__ __forceinline__ uint64_t site_key(uint32_t i, uint32_t k0, uint32_t k
 constexpr int kInitThreads = 1024;
 constexpr int kInitMaxThresholds = 7;   // species 2..8 use the fast path
 
+constexpr int kInitBins = 4096;    // first pass: histogram of the top 12 key bits
+constexpr int kInitBinCap = 256;   // keys of one threshold's bin kept for the exact selection
+
 __device__ void init_config_block(uint32_t N, int S, const Cum& cum, uint32_t k0, uint32_t k1,
                                   uint8_t* __restrict__ types) {
     __shared__ uint32_t hist[kInitMaxThresholds][256];
     __shared__ uint64_t prefix[kInitMaxThresholds];
     __shared__ uint64_t remaining[kInitMaxThresholds];
     __shared__ int active[kInitMaxThresholds];
+    // bin counts, then (same memory) the keys of each threshold's bin
+    __shared__ __align__(16) uint64_t bins_raw[kInitBins / 2];
+    __shared__ uint32_t bin_of[kInitMaxThresholds], in_bin[kInitMaxThresholds];
+    __shared__ int overflow;
     const int nt = S - 1;
-    const int tid = threadIdx.x;
+    const int tid = threadIdx.x, T = blockDim.x;
     if (tid < nt) {
         const int64_t rank = cum.v[tid + 1];
         active[tid] = rank < (int64_t)N;
         prefix[tid] = 0;
         remaining[tid] = (uint64_t)rank;
+        in_bin[tid] = 0;
     }
-    for (int pass = 0; pass < 8; ++pass) {
+    if (tid == 0) overflow = 0;
+    // Two sweeps find the thresholds exactly: the bin (top 12 key bits) holding each threshold's
+    // rank, then the keys of that bin, ranked among themselves.  A bin with more keys than the
+    // buffer holds (never for random keys at these sizes) sends the block to the radix select below.
+    uint32_t* bins = reinterpret_cast<uint32_t*>(bins_raw);
+    for (int b = tid; b < kInitBins; b += T) bins[b] = 0u;
+    __syncthreads();
+    for (uint32_t i = tid; i < N; i += T) atomicAdd(&bins[(uint32_t)(site_key(i, k0, k1) >> 52)], 1u);
+    __syncthreads();
+    if (tid < 32) {
+        // one warp: running prefix over the bins, 32 at a time; each threshold finds its bin
+        uint64_t base = 0;
+        for (int b0 = 0; b0 < kInitBins; b0 += 32) {
+            const uint32_t cnt = bins[b0 + tid];
+            uint32_t incl = cnt;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t t = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+                if (tid >= o) incl += t;
+            }
+            const uint64_t lo = base + (incl - cnt), hi = base + incl;   // ranks [lo, hi) in bin b0 + tid
+            for (int s = 0; s < nt; ++s)
+                if (active[s] && remaining[s] >= lo && remaining[s] < hi) {
+                    bin_of[s] = (uint32_t)(b0 + tid);
+                    prefix[s] = remaining[s] - lo;   // rank inside the bin (reused below)
+                }
+            base += __shfl_sync(0xFFFFFFFFu, incl, 31);
+        }
+    }
+    __syncthreads();
+    uint64_t* keys = bins_raw;   // [nt][kInitBinCap]
+    for (uint32_t i = tid; i < N; i += T) {
+        const uint64_t key = site_key(i, k0, k1);
+        const uint32_t b = (uint32_t)(key >> 52);
+        for (int s = 0; s < nt; ++s)
+            if (active[s] && b == bin_of[s]) {
+                const uint32_t x = atomicAdd(&in_bin[s], 1u);
+                if (x < (uint32_t)kInitBinCap) keys[s * kInitBinCap + x] = key;
+                else overflow = 1;
+            }
+    }
+    __syncthreads();
+    if (!overflow) {
+        for (int s = 0; s < nt; ++s) {
+            if (!active[s]) continue;
+            const uint32_t n = in_bin[s];
+            const uint64_t want = prefix[s];
+            for (uint32_t x = tid; x < n; x += T) {
+                const uint64_t kx = keys[s * kInitBinCap + x];
+                uint32_t r = 0;
+                for (uint32_t y = 0; y < n; ++y) r += keys[s * kInitBinCap + y] < kx ? 1u : 0u;
+                if (r == want) remaining[s] = kx;   // the threshold key (unique: keys are distinct)
+            }
+        }
+        __syncthreads();
+        if (tid < nt && active[tid]) prefix[tid] = remaining[tid];
+        __syncthreads();
+    } else {
+        if (tid < nt) {
+            prefix[tid] = 0;
+            remaining[tid] = (uint64_t)cum.v[tid + 1];
+        }
+        __syncthreads();
+    }
+    for (int pass = 0; pass < (overflow ? 8 : 0); ++pass) {
         const int shift = 56 - 8 * pass;
         for (int i = tid; i < kInitMaxThresholds * 256; i += blockDim.x) (&hist[0][0])[i] = 0;
         __syncthreads();

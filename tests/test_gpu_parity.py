@@ -41,6 +41,7 @@ def composition(N, S, rng, lo=1):
     (FCC, (3, 5, 7), [420], 2),                            # one species
     (FCC, (5, 5, 3), [38, 37, 37, 37, 37, 37, 37, 40], 9),  # eight species, ragged
     (BCC, (4, 4, 4), [13] * 9 + [11], 4),                  # more than eight species
+    (FCC, (64, 64, 64), [262144] * 4, 6),                   # ~256 keys per 12-bit bin: buffer overflow path
 ])
 def test_init_config_matches_oracle(kind, L, n_per, seed):
     got = G.gpu_init(kind, L, 1, n_per, seed)
