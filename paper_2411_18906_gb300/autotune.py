@@ -66,7 +66,7 @@ def tune(cells, trials: int, accept_mode: int = 0, sample: int = 48, use_cache: 
     ({bucket: (K, threads)}, report)."""
     import torch
     gpu = torch.cuda.get_device_name(0)
-    key = f"v2|{gpu}|{trials}|{accept_mode}|{len(cells)}|{CANDIDATE_K}|{CANDIDATE_THREADS}"
+    key = f"v3|{gpu}|{trials}|{accept_mode}|{len(cells)}|{CANDIDATE_K}|{CANDIDATE_THREADS}"
     path = _cache_path()
     cache = {}
     if use_cache and os.path.exists(path):
@@ -96,7 +96,9 @@ def tune(cells, trials: int, accept_mode: int = 0, sample: int = 48, use_cache: 
         report[str(b)] = {"sites": list(BUCKETS[b]), "cells_sampled": len(pick),
                           "trials_per_s": {f"{k}x{t}": v for (k, t), v in rates.items()},
                           "K": best[0], "threads": best[1], "K_tested": feasible,
-                          "bracketed": feasible[0] < best[0] < feasible[-1]}
+                          "bracketed": feasible[0] < best[0] < feasible[-1],
+                          # the grid goes on past the chosen K, but no larger K fits a CTA's shared memory
+                          "at_shared_memory_limit": best[0] == feasible[-1] and max(CANDIDATE_K) > feasible[-1]}
     if use_cache:
         cache[key] = {"choice": {str(b): list(k) for b, k in choice.items()}, "report": report}
         try:
