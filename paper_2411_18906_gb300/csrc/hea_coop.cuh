@@ -1347,9 +1347,12 @@ __device__ void run_coop_chain(const ChainDesc& d, uint8_t* smem, ChainShared& s
                 if (eligible(m.qD[q], null_move, c.thr)) apply_slot<BITS>(d, m, sh, c, q);
             }
         } else {
+            // No records: nothing to walk; no accepted swap: the coefficients and the fixed-point
+            // table of this step stay those of the next one.
             const int ne = sh.qn;
-            coop_walk<KIND, BITS>(d, m, sh, c, ne);
-            coop_after_walk(d, m, sh, c);
+            if (ne > 0) coop_walk<KIND, BITS>(d, m, sh, c, ne);
+            __syncthreads();
+            if (sh.n_acc > 0) coop_after_walk(d, m, sh, c);
         }
         __syncthreads();
         bookkeeping(d, sh, sh.pub_stop != 0);
