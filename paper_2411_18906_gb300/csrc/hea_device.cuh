@@ -291,6 +291,63 @@ __device__ __forceinline__ void neighbour_histogram_at(const Geo& g, int X, int 
     all_shells<KIND, R, MX, EXCL, H>(ax, excl, onehot, h, M, std::make_integer_sequence<int, MX>{});
 }
 
+// Species packed BITS < 8 to a byte (site i in bits BITS (i mod 8/BITS) of byte i / (8/BITS)) with
+// Lx a multiple of 8/BITS: every y and z index term is then a multiple of 8/BITS, so the byte and
+// the bit offset of a neighbour split into per-axis parts, and a gather is two additions, a load,
+// a shift and a mask.
+template <int KIND, int R, int BITS>
+struct PackedAxisTable {
+    static constexpr int lg = BITS == 4 ? 1 : 2;   // log2 of the sites per byte
+    int bx[2 * R + 1], sx[2 * R + 1], by[2 * R + 1], bz[2 * R + 1];
+
+    __device__ __forceinline__ void build(const Geo& g, int X, int Y, int Z) {
+        AxisTable<KIND, R> ax;
+        ax.build(g, X, Y, Z);
+#pragma unroll
+        for (int d = 0; d < 2 * R + 1; ++d) {
+            bx[d] = ax.x[d] >> lg;
+            sx[d] = (ax.x[d] & ((1 << lg) - 1)) * BITS;
+            by[d] = ax.y[d] >> lg;
+            bz[d] = ax.z[d] >> lg;
+        }
+    }
+};
+
+template <int KIND, int R, int BITS, int V, typename H>
+__device__ __forceinline__ H packed_increment(const PackedAxisTable<KIND, R, BITS>& ax, const uint8_t* __restrict__ types) {
+    constexpr int dx = ShellsOf<KIND>::table.v[V][0] + R;
+    constexpr int dy = ShellsOf<KIND>::table.v[V][1] + R;
+    constexpr int dz = ShellsOf<KIND>::table.v[V][2] + R;
+    const uint32_t y = ((uint32_t)types[ax.bx[dx] + ax.by[dy] + ax.bz[dz]] >> ax.sx[dx]) & ((1u << BITS) - 1u);
+    return (H)1 << (8 * y);
+}
+
+template <int KIND, int R, int BITS, int FIRST, typename H, int... I>
+__device__ __forceinline__ H packed_shell_sum(const PackedAxisTable<KIND, R, BITS>& ax, const uint8_t* __restrict__ types,
+                                              std::integer_sequence<int, I...>) {
+    return ((H)0 + ... + packed_increment<KIND, R, BITS, FIRST + I, H>(ax, types));
+}
+
+template <int KIND, int R, int BITS, int MX, typename H, int... K>
+__device__ __forceinline__ void packed_all_shells(const PackedAxisTable<KIND, R, BITS>& ax, const uint8_t* __restrict__ types,
+                                                  H (&h)[MX], int M, std::integer_sequence<int, K...>) {
+    ((h[K] = (K < M) ? packed_shell_sum<KIND, R, BITS, ShellsOf<KIND>::table.first[K], H>(
+                           ax, types, std::make_integer_sequence<int, ShellsOf<KIND>::table.z[K]>{})
+                     : (H)0),
+     ...);
+}
+
+// Full neighbour histogram (no site skipped) of the site at (X, Y, Z) from packed species; needs
+// BITS < 8 and Lx a multiple of 8 / BITS.
+template <int KIND, int MX, int BITS, typename H>
+__device__ __forceinline__ void neighbour_histogram_packed(const Geo& g, int X, int Y, int Z,
+                                                           const uint8_t* __restrict__ types, H (&h)[MX], int M) {
+    constexpr int R = shell_reach<KIND, MX>();
+    PackedAxisTable<KIND, R, BITS> ax;
+    ax.build(g, X, Y, Z);
+    packed_all_shells<KIND, R, BITS, MX, H>(ax, types, h, M, std::make_integer_sequence<int, MX>{});
+}
+
 // The same for a site index, 64-bit fields, skipping `excl`.
 template <int KIND, int MX, typename OneHot>
 __device__ __forceinline__ void neighbour_histogram_upto(const Geo& g, uint32_t site, uint32_t excl, OneHot onehot,

@@ -338,6 +338,7 @@ struct ChainCtx {
     int qcap;    // candidate slots in shared memory
     int r2max;   // |d|^2 of shell M, half units^2
     bool alias;  // some axis has at most reach(M) + 1 cells: two shell vectors may reach the same site
+    bool packed; // species below 8 bits and Lx a multiple of the sites per byte (split gathers)
     bool pos_thr;            // threshold > 0
     float thr_lo, thr_hi;    // binary32 neighbours of the threshold
 };
@@ -359,6 +360,7 @@ __device__ void chain_setup(const ChainDesc& d, ChainSmem& m, ChainShared& sh, C
     c.qcap = d.qcap;
     c.r2max = c_shells[KIND].radius2[d.M - 1];
     c.alias = min(d.Lx, min(d.Ly, d.Lz)) <= c_shells[KIND].reach[d.M - 1] + 1;
+    c.packed = BITS < 8 && d.Lx % (8 / BITS) == 0;
     c.pos_thr = d.threshold > 0.0;
     {
         float f = (float)d.threshold;
@@ -501,8 +503,18 @@ __device__ float score_range(const ChainDesc& d, ChainSmem& m, ChainShared& sh, 
                 neighbour_histogram_at<KIND, MX, true, uint32_t>(c.g, Xa, Ya, Za, b, onehot32, ha, M);
                 neighbour_histogram_at<KIND, MX, true, uint32_t>(c.g, Xb, Yb, Zb, a, onehot32, hb, M);
             } else {
-                neighbour_histogram_at<KIND, MX, false, uint32_t>(c.g, Xa, Ya, Za, 0u, onehot32, ha, M);
-                neighbour_histogram_at<KIND, MX, false, uint32_t>(c.g, Xb, Yb, Zb, 0u, onehot32, hb, M);
+                bool done = false;
+                if constexpr (BITS < 8) {
+                    if (c.packed) {
+                        neighbour_histogram_packed<KIND, MX, BITS, uint32_t>(c.g, Xa, Ya, Za, m.types, ha, M);
+                        neighbour_histogram_packed<KIND, MX, BITS, uint32_t>(c.g, Xb, Yb, Zb, m.types, hb, M);
+                        done = true;
+                    }
+                }
+                if (!done) {
+                    neighbour_histogram_at<KIND, MX, false, uint32_t>(c.g, Xa, Ya, Za, 0u, onehot32, ha, M);
+                    neighbour_histogram_at<KIND, MX, false, uint32_t>(c.g, Xb, Yb, Zb, 0u, onehot32, hb, M);
+                }
                 if (near) {
 #pragma unroll
                     for (int k = 0; k < MX; ++k)
