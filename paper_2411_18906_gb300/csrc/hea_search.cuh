@@ -55,6 +55,7 @@ struct ChainShared {
     int pub_stop;            // stop bit of CTA 0's record for this step
     int n_pairs;             // walk: suspects / conflicting records / batches holding unsure candidates
     int n_edges;             // walk: conflicting record pairs
+    int asym;                // set-up: Q or the target is not symmetric
     unsigned long long maxb; // max |b| over the entries (binary64 bits)
     unsigned int wmax;       // walk: bound on the running |b| (binary32 bits)
     long long red_l[32];
@@ -180,6 +181,40 @@ __device__ __forceinline__ void score_float(int M, int S, const float* __restric
                 mag = fmaf(ax, fmaf(fabsf(fa[eA]), ax, fabsf(fb[eA])), mag);
                 mag = fmaf(ax, fmaf(fabsf(fa[eB]), ax, fabsf(fb[eB])), mag);
             }
+        }
+    }
+    D = acc;
+    err = fmaf(mag, rel, kAbsBound);
+}
+
+// The same estimate and bound when the coefficient tables are symmetric (a_ijk = a_jik and
+// b_ijk = b_jik bit for bit): the counts stay symmetric, so (i, j) and (j, i) change alike and
+// each pair enters once with weight 2 (the doubling is exact; the sum S and every term's relative
+// rounding are unchanged, and fewer terms are added).
+__device__ __forceinline__ void score_float_sym(int M, int S, const float* __restrict__ fa,
+                                                const float* __restrict__ fb, int A, int B, const uint64_t* gb,
+                                                float rel, float& D, float& err) {
+    float acc = 0.f, mag = 0.f;
+    auto term = [&](int e, float x, float wgt) {
+        const float ax = fabsf(x);
+        acc = fmaf(wgt * x, fmaf(fa[e], x, fb[e]), acc);
+        mag = fmaf(wgt * ax, fmaf(fabsf(fa[e]), ax, fabsf(fb[e])), mag);
+    };
+#pragma unroll
+    for (int k = 0; k < kMaxShells; ++k) {
+        if (k >= M) break;
+        const uint64_t g_k = gb[k];
+        const int base = k * S * S;
+        const int gA = g_of(g_k, A), gB = g_of(g_k, B);
+        if (gA != 0) term(base + A * S + A, (float)(2 * gA), 1.0f);       // dN_AA = 2 g_A
+        if (gB != 0) term(base + B * S + B, (float)(-2 * gB), 1.0f);      // dN_BB = -2 g_B
+        if (gB != gA) term(base + A * S + B, (float)(gB - gA), 2.0f);     // dN_AB = dN_BA = g_B - g_A
+        for (int y = 0; y < S; ++y) {
+            if (y == A || y == B) continue;
+            const int gy = g_of(g_k, y);
+            if (gy == 0) continue;
+            term(base + A * S + y, (float)gy, 2.0f);    // dN_Ay = dN_yA = g_y
+            term(base + B * S + y, (float)(-gy), 2.0f); // dN_By = dN_yB = -g_y
         }
     }
     D = acc;
@@ -339,6 +374,7 @@ struct ChainCtx {
     int r2max;   // |d|^2 of shell M, half units^2
     bool alias;  // some axis has at most reach(M) + 1 cells: two shell vectors may reach the same site
     bool packed; // species below 8 bits and Lx a multiple of the sites per byte (split gathers)
+    bool sym;    // Q and the target symmetric bit for bit: every coefficient table stays symmetric
     bool pos_thr;            // threshold > 0
     float thr_lo, thr_hi;    // binary32 neighbours of the threshold
 };
@@ -439,8 +475,18 @@ __device__ void chain_setup(const ChainDesc& d, ChainSmem& m, ChainShared& sh, C
     }
     if (d.accept_mode == 1 && clear_bitmap)
         for (uint32_t i = tid; i < (N + 31) / 32; i += T) m.bitmap[i] = 0;
+    if (tid == 0) sh.asym = 0;
+    __syncthreads();
+    for (int e = tid; e < E; e += T) {
+        const int k = e / (S * S), i = (e / S) % S, j = e % S;
+        const int f = (k * S + j) * S + i;
+        if (__double_as_longlong(m.Q[e]) != __double_as_longlong(m.Q[f]) ||
+            __double_as_longlong(m.tgt[e]) != __double_as_longlong(m.tgt[f]))
+            sh.asym = 1;
+    }
     __syncthreads();
     c.use_filter = sh.use_filter != 0;
+    c.sym = sh.asym == 0;
 }
 
 // Minimum-image squared length (half units^2) of a displacement between two sites of the cell.
@@ -558,7 +604,10 @@ __device__ float score_range(const ChainDesc& d, ChainSmem& m, ChainShared& sh, 
                 hi = 0.f;
             } else {
                 float Dt, err;
-                score_float(M, c.S, m.fa, m.fb, A, B, gb, c.rel, Dt, err);
+                if (c.sym)
+                    score_float_sym(M, c.S, m.fa, m.fb, A, B, gb, c.rel, Dt, err);
+                else
+                    score_float(M, c.S, m.fa, m.fb, A, B, gb, c.rel, Dt, err);
                 hi = __fadd_ru(Dt, err);
                 lo = __fadd_rd(Dt, -err);
             }
