@@ -551,7 +551,18 @@ __device__ float score_range(const ChainDesc& d, ChainSmem& m, ChainShared& sh, 
             } else {
                 bool done = false;
                 if constexpr (BITS < 8) {
-                    if (c.packed) {
+                    if (c.packed && M <= 3) {
+                        // shells 1-3 only: axis tables of reach 2 and no code for shells 4-5
+                        uint32_t h3a[3], h3b[3];
+                        neighbour_histogram_packed<KIND, 3, BITS, uint32_t>(c.g, Xa, Ya, Za, m.types, h3a, M);
+                        neighbour_histogram_packed<KIND, 3, BITS, uint32_t>(c.g, Xb, Yb, Zb, m.types, h3b, M);
+#pragma unroll
+                        for (int k = 0; k < MX; ++k) {
+                            ha[k] = k < 3 ? h3a[k < 3 ? k : 0] : 0u;
+                            hb[k] = k < 3 ? h3b[k < 3 ? k : 0] : 0u;
+                        }
+                        done = true;
+                    } else if (c.packed) {
                         neighbour_histogram_packed<KIND, MX, BITS, uint32_t>(c.g, Xa, Ya, Za, m.types, ha, M);
                         neighbour_histogram_packed<KIND, MX, BITS, uint32_t>(c.g, Xb, Yb, Zb, m.types, hb, M);
                         done = true;
