@@ -61,12 +61,28 @@ def _time_batch(torch, cells, K, trials, accept_mode, threads=0, repeats=2):
     return best
 
 
+def _fits(torch, cells, K, threads, trials, accept_mode):
+    """True when a batch plan of `cells` with K candidates and `threads` per CTA fits shared memory
+    (planned on the host; nothing is launched)."""
+    params = [hea.search_params(K, max(1, trials // K), accept_mode=accept_mode, seed=1, threads=threads)
+              for _ in cells]
+    res = torch.zeros(len(cells) * hea.RESULT_BYTES, dtype=torch.uint8, device="cuda")
+    try:
+        hea.BatchPlan([l for l, _, _, _ in cells], [o for _, o, _, _ in cells], params, [t for _, _, t, _ in cells],
+                      [c for _, _, _, c in cells], res)
+    except hea.HeaError as e:
+        if e.status == hea.HEA_ENOMEM:
+            return False
+        raise
+    return True
+
+
 def tune(cells, trials: int, accept_mode: int = 0, sample: int = 48, use_cache: bool = True):
     """cells: list of (Lattice, Objective, types tensor, counts tensor).  Returns
     ({bucket: (K, threads)}, report)."""
     import torch
     gpu = torch.cuda.get_device_name(0)
-    key = f"v3|{gpu}|{trials}|{accept_mode}|{len(cells)}|{CANDIDATE_K}|{CANDIDATE_THREADS}"
+    key = f"v4|{gpu}|{trials}|{accept_mode}|{len(cells)}|{CANDIDATE_K}|{CANDIDATE_THREADS}"
     path = _cache_path()
     cache = {}
     if use_cache and os.path.exists(path):
@@ -90,7 +106,14 @@ def tune(cells, trials: int, accept_mode: int = 0, sample: int = 48, use_cache: 
                 dt = _time_batch(torch, pick, K, trials, accept_mode, threads)
                 if dt is not None:
                     rates[(K, threads)] = len(pick) * (trials // K) * K / dt
-        best = max(rates, key=rates.get)
+        # the fastest pair on the sample whose candidate slots fit every cell of the bucket
+        best = None
+        for pair in sorted(rates, key=rates.get, reverse=True):
+            if _fits(torch, members, pair[0], pair[1], trials, accept_mode):
+                best = pair
+                break
+        if best is None:
+            raise RuntimeError(f"no candidate (K, threads) fits every cell of size bucket {b}")
         feasible = sorted({k for k, _ in rates})
         choice[b] = best
         report[str(b)] = {"sites": list(BUCKETS[b]), "cells_sampled": len(pick),
