@@ -1289,15 +1289,16 @@ __device__ void run_coop_chain(const ChainDesc& d, uint8_t* smem, ChainShared& s
             __syncthreads();
         } else {
             // The slice in chunks: the best `top` so far are carried into the next chunk's slots.
+            // (nothing queued beyond the carried winners: they stay the selection, in order)
             __syncthreads();
-            n_pub = coop_select<BITS>(m, sh, c, top, 0);
+            n_pub = (sh.qn > 0) ? coop_select<BITS>(m, sh, c, top, 0) : 0;
             for (uint32_t c0 = first_end; c0 < k_hi; c0 += (uint32_t)d.chunk) {
                 carry_winners(m, c, n_pub);
                 if (tid == 0) sh.qn = n_pub;
                 __syncthreads();
                 score_range<KIND, BITS>(d, m, sh, c, step, c0, min(k_hi, c0 + (uint32_t)d.chunk));
                 __syncthreads();
-                n_pub = coop_select<BITS>(m, sh, c, top, n_pub);
+                if (sh.qn > n_pub) n_pub = coop_select<BITS>(m, sh, c, top, n_pub);
             }
         }
         // Publish this CTA's records for the step (double-buffered by step parity), then the tag.
