@@ -388,31 +388,34 @@ __global__ void __launch_bounds__(kCountThreads) counts_planes_kernel(Geo g, int
     for (int i = threadIdx.x; i < nwarp * (E + S); i += blockDim.x) wh[i] = 0;
     if (threadIdx.x == 0) invalid = 0;
     __syncthreads();
-    // bit planes: one warp per row, two halves of 32 cells; each warp loads 8 rows before it
-    // builds their planes, so that 8 row loads are in flight at once
-    constexpr int RU = 8;
+    // bit planes: one thread per row (rows are x-contiguous: ((b Lz + cz) Ly + cy) Lx), read four
+    // cells at a time when rows start on 4-byte boundaries
     bool bad = false;
-    for (int r0 = warp * RU; r0 < R; r0 += nwarp * RU) {
-        int y0[RU], y1[RU];
+    const bool words = (Lx % 4 == 0) && ((reinterpret_cast<uintptr_t>(t) & 3u) == 0u);
+    for (int r = threadIdx.x; r < R; r += blockDim.x) {
+        W pl[S];
 #pragma unroll
-        for (int u = 0; u < RU; ++u) {
-            const int r = r0 + u;
-            const uint8_t* row = t + (size_t)r * Lx;   // rows are x-contiguous: ((b Lz + cz) Ly + cy) Lx
-            y0[u] = (r < R && lane < Lx) ? row[lane] : 0;
-            y1[u] = (r < R && lane + 32 < Lx) ? row[lane + 32] : 0;
-        }
+        for (int y = 0; y < S; ++y) pl[y] = W(0);
+        auto cell = [&](int v, int x) {
+            const W bit = W(1) << x;
 #pragma unroll
-        for (int u = 0; u < RU; ++u) {
-            const int r = r0 + u;
-            if (r >= R) break;   // warp-uniform
-            bad = bad || (lane < Lx && y0[u] >= S) || (lane + 32 < Lx && y1[u] >= S);
+            for (int y = 0; y < S; ++y)
+                if (v == y) pl[y] |= bit;
+            bad = bad || v >= S;
+        };
+        if (words) {
+            const uint32_t* row = reinterpret_cast<const uint32_t*>(t + (size_t)r * Lx);
+            for (int x4 = 0; x4 < Lx / 4; ++x4) {
+                const uint32_t w4 = __ldg(row + x4);
 #pragma unroll
-            for (int y = 0; y < S; ++y) {
-                const uint32_t lo = __ballot_sync(0xFFFFFFFFu, lane < Lx && y0[u] == y),
-                               hi = __ballot_sync(0xFFFFFFFFu, lane + 32 < Lx && y1[u] == y);
-                if (lane == 0) planes[(size_t)y * R + r] = (W)((uint64_t)lo | ((uint64_t)hi << 32));
+                for (int q = 0; q < 4; ++q) cell((int)((w4 >> (8 * q)) & 0xFFu), 4 * x4 + q);
             }
+        } else {
+            const uint8_t* row = t + (size_t)r * Lx;
+            for (int x = 0; x < Lx; ++x) cell(__ldg(row + x), x);
         }
+#pragma unroll
+        for (int y = 0; y < S; ++y) planes[(size_t)y * R + r] = pl[y];
     }
     if (bad) invalid = 1;
     __syncthreads();
