@@ -787,9 +787,14 @@ __device__ void coop_walk(const ChainDesc& d, ChainSmem& m, ChainShared& sh, con
         const int ns = sh.n_pairs;
         const int r2max = c_shells[KIND].radius2[M - 1];
         const int PX = 2 * c.g.Lx, PY = 2 * c.g.Ly, PZ = 2 * c.g.Lz;
-        for (int x = tid; x < ns * ns; x += T) {
-            const int u = x / ns, v = x - u * ns;
-            if (u >= v) continue;
+        // pairs u < v of the suspects: row u of the strict upper triangle holds ns - 1 - u pairs
+        for (int x = tid; x < ns * (ns - 1) / 2; x += T) {
+            // invert x = u (2 ns - u - 1) / 2 + (v - u - 1): the largest u with start(u) <= x
+            int u = (int)((2.0f * ns - 1.0f - sqrtf((2.0f * ns - 1.0f) * (2.0f * ns - 1.0f) - 8.0f * x)) * 0.5f);
+            u = max(0, min(u, ns - 2));
+            while (u > 0 && u * (2 * ns - u - 1) / 2 > x) --u;
+            while (u + 1 <= ns - 2 && (u + 1) * (2 * ns - u - 2) / 2 <= x) ++u;
+            const int v = x - u * (2 * ns - u - 1) / 2 + u + 1;
             const int s0 = w.susp[u], t0 = w.susp[v];
             const int qs = s0 >> 1, qt = t0 >> 1;
             if (qs == qt) continue;
@@ -928,8 +933,14 @@ __device__ void coop_walk(const ChainDesc& d, ChainSmem& m, ChainShared& sh, con
                 if ((w.accb[q >> 5] >> (q & 31)) & 1u) {
                     store_species_atomic<BITS>(m.types, w.site[2 * q], w.spec[2 * q + 1]);
                     store_species_atomic<BITS>(m.types, w.site[2 * q + 1], w.spec[2 * q]);
-                    atomicAdd(&sh.n_acc, 1);
                 }
+            if (warp == 0) {   // accepted records: the bits of the mask
+                int n = 0;
+                for (int y = lane; y < nw; y += 32) n += __popc(w.accb[y]);
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) n += __shfl_xor_sync(0xFFFFFFFFu, n, o);
+                if (lane == 0) sh.n_acc = n;
+            }
         }
         __syncthreads();
         return;
