@@ -591,7 +591,7 @@ struct CoopWalk {
     int16_t* pos;      // [nrec][6] half-unit positions of a and b
     // (dense, site, spec, pos and conf are indexed by slot; the walk reaches them through m.order)
     uint32_t* conf;    // [nrec][nw] bit q' of row q: merged records q and q' conflict (slot space)
-    int32_t* Ptot;     // [Ep] sum over the records of |dN_e|
+    int32_t* Ptot;     // [Ep] sums over the records of the positive | negative dN_e (low | high 16 bits)
     uint32_t* accb;    // [2 nw] fast path: accepted records, then scratch (slot space)
     uint32_t* edge;    // [2 nrec] conflicting record pairs (slot << 16 | slot)
     uint32_t* cellA;   // occupancy of hashed conventional cells (one bit per hash value)
@@ -779,7 +779,8 @@ __device__ void coop_walk(const ChainDesc& d, ChainSmem& m, ChainShared& sh, con
     // P2: exact conflicts among the suspects (minimum-image distance within shell M, the same relation
     // as closed shell neighbourhoods for cells of at least two conventional cells per axis); the
     // occupancy bits are cleared for the next step.  Sure records: accepting any set of the other
-    // records shifts a record's key by 2 sum_i X(i, j), |.| <= U = 2 sum_e |a_e| |dN_j,e| sum_i |dN_i,e|;
+    // records shifts a record's key by 2 sum_i X(i, j) <= U = 2 sum_e a_e |dN_j,e| P_e, P_e the sum over
+    // the records of the changes of dN_j,e's sign;
     // a record whose step-start interval stays eligible under that shift (plus the roundings of the
     // binary64 coefficients at the running counts) is accepted unless a conflicting record before it
     // is.
@@ -817,7 +818,8 @@ __device__ void coop_walk(const ChainDesc& d, ChainSmem& m, ChainShared& sh, con
             atomicAnd(&w.cellA[hc >> 5], ~(1u << (hc & 31)));
             atomicAnd(&w.cellB[hc >> 5], ~(1u << (hc & 31)));
         }
-        // per-entry totals sum over the records of |dN_e|, in parts of the record list
+        // per-entry totals over the records of the positive and the negative count changes (low and
+        // high 16 bits: each is at most 640 x 48), in parts of the record list
         {
             const int parts = max(1, T / Ep);
             for (int x = tid; x < Ep * parts; x += T) {
@@ -825,7 +827,7 @@ __device__ void coop_walk(const ChainDesc& d, ChainSmem& m, ChainShared& sh, con
                 int sum = 0;
                 for (int q = part; q < ne; q += parts) {
                     const int v = w.dense[q * Ep + e];
-                    sum += v < 0 ? -v : v;
+                    sum += v > 0 ? v : (-v << 16);
                 }
                 if (sum) atomicAdd(&w.Ptot[e], sum);
             }
@@ -839,9 +841,13 @@ __device__ void coop_walk(const ChainDesc& d, ChainSmem& m, ChainShared& sh, con
             if (q < ne) {
                 const int8_t* row = w.dense + q * Ep;
                 for (int e = l8; e < E; e += 8) {
+                    // the accepted records' changes sum to S_e in [-Pneg_e, Ppos_e], so a_e dN S_e is at
+                    // most a_e dN Ppos_e (dN > 0) or a_e |dN| Pneg_e (dN < 0)
                     const int dl = row[e];
                     const float ad = (float)(dl < 0 ? -dl : dl);
-                    U = fmaf(fabsf(m.fa[e]) * ad, (float)w.Ptot[e], U);
+                    const int P = w.Ptot[e];
+                    const float side = (float)(dl > 0 ? (P & 0xFFFF) : (P >> 16));
+                    U = fmaf(fabsf(m.fa[e]) * ad, side, U);
                     tin = fmaf(ad, 2.0f * m.tiny[e], tin);
                 }
             }
