@@ -55,6 +55,7 @@ struct ChainShared {
     int pub_stop;            // stop bit of CTA 0's record for this step
     int n_pairs;             // walk: suspects / conflicting records / batches holding unsure candidates
     int n_edges;             // walk: conflicting record pairs
+    int win_elig;            // best-of-K: winner eligible (1), not (0), or decided on its binary64 key (-1)
     int asym;                // set-up: Q or the target is not symmetric
     unsigned long long maxb; // max |b| over the entries (binary64 bits)
     unsigned int wmax;       // walk: bound on the running |b| (binary32 bits)
@@ -657,13 +658,47 @@ __device__ __forceinline__ float block_min(float v, ChainShared& sh) {
 // A contender is a queued candidate with lo <= min(umin, threshold): the argmin, whenever it is
 // acceptable, is one of them.  Sets sh.win_q to the best slot, or -1.
 template <int BITS>
-__device__ void best_of_queue(ChainSmem& m, ChainShared& sh, const ChainCtx& c, float umin) {
+// need_key = false (single chain): with exactly one contender the argmin needs no key, and its
+// eligibility is taken from its FP32 interval when that settles it (sh.win_elig 1 / 0; -1: the
+// caller decides on the binary64 key in m.qD).
+__device__ void best_of_queue(ChainSmem& m, ChainShared& sh, const ChainCtx& c, float umin, bool need_key = true) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const double tau = c.use_filter ? fmin((double)umin, c.thr) : CUDART_INF;
     double bD = CUDART_INF;
     uint32_t bk = 0xFFFFFFFFu;
     int bq = -1;
     const int qn = sh.qn;
+    if (threadIdx.x == 0) sh.win_elig = -1;
+    if (!need_key && c.use_filter) {
+        int mine = 0, mq = -1;
+        for (int q = threadIdx.x; q < qn; q += blockDim.x)
+            if (!((double)m.qlo[q] > tau)) {
+                ++mine;
+                mq = q;
+            }
+        const int holders = __syncthreads_count(mine > 0);
+        const int several = __syncthreads_or(mine > 1);
+        if (holders == 1 && !several) {
+            if (mine == 1) {
+                sh.win_q = mq;
+                const int v = eligible_interval(m.qlo[mq], m.qhi[mq], c.pos_thr, c.thr_lo, c.thr_hi);
+                if (v >= 0) {
+                    sh.win_elig = v;
+                } else {
+                    const uint32_t a = m.qa[mq], b = m.qb[mq];
+                    const int A = load_species<BITS>(m.types, a), B = load_species<BITS>(m.types, b);
+                    m.qD[mq] = (a == b || A == B) ? 0.0 : exact_key(c.M, c.S, m.ca, m.cb, A, B, m.qg + mq * c.M);
+                }
+            }
+            __syncthreads();
+            return;
+        }
+        if (holders == 0) {
+            if (threadIdx.x == 0) sh.win_q = -1;
+            __syncthreads();
+            return;
+        }
+    }
     for (int q = threadIdx.x; q < qn; q += blockDim.x) {
         if (c.use_filter && (double)m.qlo[q] > tau) continue;
         const uint32_t a = m.qa[q], b = m.qb[q];
@@ -1542,12 +1577,13 @@ __device__ void run_chain(const ChainDesc& d, uint8_t* smem, ChainShared& sh) {
         const float my_umin = score_range<KIND, BITS>(d, m, sh, c, step, 0u, (uint32_t)c.K);
         if (d.accept_mode == 0) {
             const float umin = block_min(my_umin, sh);
-            best_of_queue<BITS>(m, sh, c, umin);
+            best_of_queue<BITS>(m, sh, c, umin, false);
             const int q = sh.win_q;
             if (q >= 0) {
                 const uint32_t a = m.qa[q], b = m.qb[q];
                 const bool null_move = (a == b) || load_species<BITS>(m.types, a) == load_species<BITS>(m.types, b);
-                if (eligible(m.qD[q], null_move, c.thr)) apply_slot<BITS>(d, m, sh, c, q);
+                const bool ok = sh.win_elig >= 0 ? (sh.win_elig == 1 && !null_move) : eligible(m.qD[q], null_move, c.thr);
+                if (ok) apply_slot<BITS>(d, m, sh, c, q);
             }
         } else {
             __syncthreads();
