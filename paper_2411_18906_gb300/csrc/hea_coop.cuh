@@ -551,14 +551,16 @@ __device__ void coop_rank(ChainSmem& m, ChainShared& sh, const ChainCtx& c, int 
                 }
             if (tid == 0) sh.n_amb = 0;
             __syncthreads();
-            for (int q = tid; q < ne; q += T) {
+            // one warp per flagged record, its lanes over the other records
+            const int lane = tid & 31, warp = tid >> 5, nw = T >> 5;
+            for (int q = warp; q < ne; q += nw) {
                 const uint32_t fq = m.qflag[q];
                 if (!(fq & 8u)) continue;
                 if (tier == 1 && !(fq & 32u)) continue;
                 const float loq = m.qlo[q], hiq = m.qhi[q];
                 uint32_t extra = 0u;
                 bool open = false;
-                for (int p = 0; p < ne; ++p) {
+                for (int p = lane; p < ne; p += 32) {
                     if (p == q || m.qhi[p] < loq || hiq < m.qlo[p]) continue;
                     const int o = slot_order<BITS>(m, c, p, q);
                     if (o < 0)
@@ -566,12 +568,17 @@ __device__ void coop_rank(ChainSmem& m, ChainShared& sh, const ChainCtx& c, int 
                     else
                         extra += (uint32_t)o;
                 }
-                if (!open) {
-                    m.acc[q] += extra;
-                    m.qflag[q] = fq & ~40u;
-                } else {
-                    m.qflag[q] = fq | 32u;
-                    sh.n_amb = 1;
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) extra += __shfl_xor_sync(0xFFFFFFFFu, extra, o);
+                open = __any_sync(0xFFFFFFFFu, open);
+                if (lane == 0) {
+                    if (!open) {
+                        m.acc[q] += extra;
+                        m.qflag[q] = fq & ~40u;
+                    } else {
+                        m.qflag[q] = fq | 32u;
+                        sh.n_amb = 1;
+                    }
                 }
             }
             __syncthreads();
