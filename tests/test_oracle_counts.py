@@ -111,3 +111,40 @@ def test_exhaustive_16_site_bcc_binary():
     # C(14, 7) = 3432 arrangements: sum = 12870 * N_A * Z_k * N_B / (N - 1).
     assert list(total_ab) == [439296, 329472, 658944]
     assert minus_one == 2   # the two B2 variants
+
+
+@pytest.mark.parametrize("kind,L,M,S", [(ind.FCC, (4, 5, 3), 3, 4), (ind.BCC, (6, 4, 5), 2, 5),
+                                        (ind.FCC, (2, 3, 2), 5, 6), (ind.BCC, (3, 3, 4), 5, 3)])
+def test_half_vectors_and_row_sums_give_the_counts(kind, L, M, S):
+    """The bit-plane recount's algebra, checked on the oracle's neighbour lists: the vector -v counts
+    (j, i) where v counts (i, j), so N_ij = sum over the lexicographically positive half of each
+    shell's vectors of c_ij + c_ji; each row of N^(k) sums to N_i Z_k, which gives the last species."""
+    N = oracle.num_sites(kind, L)
+    rng = np.random.default_rng(3 * M + S)
+    t = rng.integers(0, S, N).astype(np.uint8)
+    Z, _, vecs = oracle.shells(kind, M)
+    nbr = oracle.neighbours(kind, L, M)
+    pos = oracle.positions(kind, L)
+    period = 2 * np.array(L)
+    # the neighbour columns follow the shell vectors
+    for s in (0, N // 2, N - 1):
+        for v in range(len(vecs)):
+            assert np.array_equal((pos[s] + vecs[v]) % period, pos[nbr[s, v]] % period)
+    want = oracle.counts(kind, L, M, S, t)
+    n_i = np.bincount(t, minlength=S)
+    start = 0
+    for k in range(M):
+        vk = vecs[start:start + Z[k]]
+        half = [start + v for v in range(Z[k]) if tuple(vk[v]) > (0, 0, 0)]
+        assert len(half) * 2 == Z[k]
+        c = np.zeros((S, S), np.int64)
+        for v in half:
+            np.add.at(c, (t, t[nbr[:, v]]), 1)
+        got = np.zeros((S, S), np.int64)
+        got[:S - 1, :S - 1] = (c + c.T)[:S - 1, :S - 1]
+        for i in range(S - 1):
+            got[i, S - 1] = n_i[i] * Z[k] - got[i, :S - 1].sum()
+            got[S - 1, i] = got[i, S - 1]
+        got[S - 1, S - 1] = n_i[S - 1] * Z[k] - got[S - 1, :S - 1].sum()
+        assert np.array_equal(got, want[k]), k
+        start += Z[k]

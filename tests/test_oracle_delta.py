@@ -84,3 +84,42 @@ def test_delta_matches_g_vector_rule_on_a_bond():
             assert dN[0, k, A, A] == 2 * g[A]
             assert dN[0, k, B, B] == -2 * g[B]
             assert dN[0, k, A, B] == g[B] - g[A] == dN[0, k, B, A]
+
+
+def test_symmetric_screen_covers_every_changed_entry():
+    """The symmetric FP32 screen adds (A, A), (B, B), 2 (A, B) and 2 (A, y), 2 (B, y) for the other
+    species y: with symmetric coefficients this equals the sum over every ordered entry of
+    dN (a dN + b), exactly (rational arithmetic), because the count changes of a swap are symmetric
+    and vanish outside rows and columns A and B."""
+    from fractions import Fraction
+    kind, L, M, S = ind.FCC, (3, 4, 3), 3, 4
+    N = oracle.num_sites(kind, L)
+    rng = np.random.default_rng(17)
+    t = rng.integers(0, S, N).astype(np.uint8)
+    n_per = np.bincount(t, minlength=S)
+    cnt = oracle.counts(kind, L, M, S, t)
+    pairs = rng.integers(0, N, (200, 2))
+    _, dN, null = oracle.delta_swap(kind, L, M, n_per, np.ones(M), np.zeros((M, S, S)), t, cnt, pairs)
+    a = [[[Fraction(int(x), 97) for x in row] for row in rng.integers(1, 50, (S, S))] for _ in range(M)]
+    b = [[[Fraction(int(x), 89) for x in row] for row in rng.integers(-40, 40, (S, S))] for _ in range(M)]
+    for k in range(M):
+        for i in range(S):
+            for j in range(i):
+                a[k][i][j] = a[k][j][i]
+                b[k][i][j] = b[k][j][i]
+    term = lambda k, i, j: dN_k[i, j] * (a[k][i][j] * dN_k[i, j] + b[k][i][j])
+    checked = 0
+    for p in range(len(pairs)):
+        if null[p]:
+            continue
+        A, B = int(t[pairs[p, 0]]), int(t[pairs[p, 1]])
+        full = half = Fraction(0)
+        for k in range(M):
+            dN_k = dN[p, k].astype(np.int64)
+            assert np.array_equal(dN_k, dN_k.T)
+            full += sum(term(k, i, j) for i in range(S) for j in range(S))
+            half += term(k, A, A) + term(k, B, B) + 2 * term(k, A, B)
+            half += sum(2 * (term(k, A, y) + term(k, B, y)) for y in range(S) if y not in (A, B))
+        assert full == half
+        checked += 1
+    assert checked > 100
