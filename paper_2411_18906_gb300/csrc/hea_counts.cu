@@ -9,6 +9,38 @@ namespace hea {
 
 static __constant__ ShellTable c_shells[2] = {build_shell_table(kFCC), build_shell_table(kBCC)};
 
+// The lexicographically positive half of every shell's vectors (the shells are centrosymmetric).
+struct HalfShells {
+    int first[kMaxShells + 1];   // index of the first half vector of shell k
+    signed char v[48][3];
+};
+
+__host__ __device__ constexpr HalfShells build_half_shells(int kind) {
+    const ShellTable t = build_shell_table(kind);
+    HalfShells h{};
+    int n = 0;
+    for (int k = 0; k < kMaxShells; ++k) {
+        h.first[k] = n;
+        for (int v = t.first[k]; v < t.first[k + 1]; ++v) {
+            const int x = t.v[v][0], y = t.v[v][1], z = t.v[v][2];
+            if (x > 0 || (x == 0 && (y > 0 || (y == 0 && z > 0)))) {
+                h.v[n][0] = t.v[v][0];
+                h.v[n][1] = t.v[v][1];
+                h.v[n][2] = t.v[v][2];
+                ++n;
+            }
+        }
+    }
+    h.first[kMaxShells] = n;
+    return h;
+}
+
+static __constant__ HalfShells c_half[2] = {build_half_shells(kFCC), build_half_shells(kBCC)};
+static_assert(2 * build_half_shells(kFCC).first[kMaxShells] == build_shell_table(kFCC).first[kMaxShells],
+              "every FCC shell splits into two halves");
+static_assert(2 * build_half_shells(kBCC).first[kMaxShells] == build_shell_table(kBCC).first[kMaxShells],
+              "every BCC shell splits into two halves");
+
 // ------------------------------------------------------------------------------------------------
 // Initial configuration (Sec. 4.1: random first solutions) with an exact composition.
 // Site i has the unique key (r0 << 32 | i), r0 = Philox(i, 0, 0, 0).  The site of rank r gets
@@ -336,11 +368,6 @@ __device__ __forceinline__ W rot_row(W w, int s, int Lx, W mask) {
 __device__ __forceinline__ int popc_w(uint32_t w) { return __popc(w); }
 __device__ __forceinline__ int popc_w(uint64_t w) { return __popcll(w); }
 
-// Half of a centrosymmetric shell: the vectors that are lexicographically positive.
-__device__ __forceinline__ bool half_vector(const signed char* v) {
-    return v[0] > 0 || (v[0] == 0 && (v[1] > 0 || (v[1] == 0 && v[2] > 0)));
-}
-
 // Target row and x shift of shell vector V from row (b, cz, cy).
 template <int KIND>
 __device__ __forceinline__ int vector_row(const signed char* V, int b, int cz, int cy, int Ly, int Lz, int& dcx) {
@@ -420,6 +447,7 @@ __global__ void __launch_bounds__(kCountThreads) counts_planes_kernel(Geo g, int
     if (bad) invalid = 1;
     __syncthreads();
     const ShellTable& TAB = c_shells[KIND];
+    const HalfShells& HALF = c_half[KIND];
     const Divider dLy = make_divider((uint32_t)Ly), dLz = make_divider((uint32_t)Lz);
     auto row_of = [&](int r, int& b, int& cz, int& cy) {
         const uint32_t t2 = divide((uint32_t)r, dLy);
@@ -446,10 +474,9 @@ __global__ void __launch_bounds__(kCountThreads) counts_planes_kernel(Geo g, int
                     for (int a = 0; a < SM1; ++a) ni[a] += popc_w(own[a]);
                     ni[SM1] += popc_w(planes[(size_t)SM1 * R + r]);
                 }
-                for (int v = TAB.first[k]; v < TAB.first[k + 1]; ++v) {
-                    if (!half_vector(TAB.v[v])) continue;
+                for (int v = HALF.first[k]; v < HALF.first[k + 1]; ++v) {
                     int dcx;
-                    const int r2 = vector_row<KIND>(TAB.v[v], b, cz, cy, Ly, Lz, dcx);
+                    const int r2 = vector_row<KIND>(HALF.v[v], b, cz, cy, Ly, Lz, dcx);
                     W nb[SM1];
 #pragma unroll
                     for (int y = 0; y < SM1; ++y) nb[y] = rot_row<W>(planes[(size_t)y * R + r2], dcx, Lx, mask);
